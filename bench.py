@@ -1,0 +1,308 @@
+#!/usr/bin/env python3
+"""Throughput of the colour-coding DP on GB300 (one JSON line on stdout).
+
+Workload: Chung-Lu power-law graph, n = 1,000,000, mean degree 16, degree
+exponent 2.1 (seeded, synthetic; the paper's SNAP graphs are not available),
+queries C6 and "glasses" (two triangles joined by a 2-edge path, k = 7),
+plain form: one colouring per query per launch sequence.  A step counts both
+queries under one fresh colouring each.  The graph is resident in HBM before
+the timed region; the timed region covers K steps, each bracketed by CUDA
+events on the library's stream, with a 256 MB L2 flush between steps outside
+the events.
+
+value: G edge-subset updates/s over all ranks, where the updates of a step
+are the structural work the library reports (cc_work_units, independent of
+the colouring).  Under torchrun each rank counts its own colourings on its
+own copy of the graph (colourings are independent; no data-path
+collective), so scaling is weak.
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "colorful-count DP G edge·subset updates/s + colorings/s, batched vs plain; p99"
+UNIT = "G edge-subset updates/s"
+WORKLOAD = {"graph": "chung_lu", "n": 1_000_000, "mean_deg": 16, "gamma": 2.1, "seed": 2,
+            "queries": ["C6", "glasses"], "form": "plain", "colourings_per_query_per_step": 1}
+COLOR_SEED = 1
+FLUSH_BYTES = 256 << 20
+
+
+def workload_name():
+    w = WORKLOAD
+    return (f"chung_lu n={w['n']} mean_deg={w['mean_deg']} gamma={w['gamma']} seed={w['seed']}; "
+            f"queries C6 + glasses; plain form, 1 colouring per query per step")
+
+
+def make_graph():
+    import graphgen as gg
+    w = WORKLOAD
+    return gg.chung_lu(w["n"], w["mean_deg"], w["gamma"], w["seed"])
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ----------------------------------- CPU oracle -----------------------------------
+def oracle_sample(g, seconds_target: float, seed: int = 0):
+    """Time the oracle's DP for C6 on a random sample of sources (highest
+    cycle vertices), sized to about `seconds_target` seconds.  Returns
+    (units of the sample, seconds, number of sources)."""
+    import numpy as np
+
+    import graphgen as gg
+    import oracle as O
+    k, e = gg.query("C6")
+    col = O.colors(COLOR_SEED, 0, g.n, k)
+    rng = np.random.default_rng(seed)
+    p = 2e-4
+    best = None
+    for _ in range(4):
+        filt = (rng.random(g.n) < p).astype(np.uint8)
+        t = {}
+        O.dp_count(g, k, e, col, root_filter=filt, timing=t)
+        secs = max(t["dp_seconds"], 1e-6)
+        units = O.cycle_units(g, 6, k, source_filter=filt)
+        best = (units, secs, int(filt.sum()))
+        if secs >= seconds_target * 0.5:
+            break
+        p = min(1.0, p * min(50.0, seconds_target / secs))
+    return best
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    g = make_graph()
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for w in range(args.warmup):
+        oracle_sample(g, min(per_step, 2.0), seed=100 + w)
+    units_tot, secs_tot, srcs = 0.0, 0.0, 0
+    for s in range(args.steps):
+        u, sec, n = oracle_sample(g, per_step, seed=s)
+        units_tot += u
+        secs_tot += sec
+        srcs += n
+    value = units_tot / secs_tot / 1e9
+    sample = (f"C6 DP restricted to {srcs} random highest-cycle-vertex sources over {args.steps} steps "
+              f"(~{per_step:.0f} s of single-thread CPU each); glasses' table stages cannot be sampled by "
+              f"source and are not timed")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs_tot / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": workload_name(), **WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------ GPU arm ------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    import paper_1602_04478_gb300 as P
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    g = make_graph()
+    ctx = P.Context(local)
+    gid = ctx.load_graph(g)
+    qids = {name: ctx.set_query(*gg.query(name)) for name in WORKLOAD["queries"]}
+    P.cc_set_coloring_seed(ctx.h, COLOR_SEED)
+    units = {name: P.cc_work_units(ctx.h, gid, q) for name, q in qids.items()}
+    units_step = sum(units.values())
+    trial_base = rank * 1_000_000
+
+    def step(i):
+        out = {}
+        for name, q in qids.items():
+            col, _, _ = ctx.count(gid, q, trial_base + i, 1)
+            out[name] = int(col[0])
+        return out
+
+    for w in range(args.warmup):
+        step(10_000 + w)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
+    stream = ctx.stream
+    P.cc_set_timing(ctx.h, True)
+    P.cc_reset_timing(ctx.h)
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    evs = []
+    counts = []
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        counts.append(step(i))
+        b.record(stream)
+        evs.append((a, b))
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    kern = P.cc_get_timing(ctx.h)
+    P.cc_set_timing(ctx.h, False)
+    if dist is not None:
+        t = torch.tensor([ms], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = units_step * args.steps * world / (ms / 1e3) / 1e9
+    colourings = len(qids) * args.steps * world / (ms / 1e3)
+    launches = sum(c for _, c in kern.values())
+
+    # dominant kernel and its roofline (algorithmic bytes: 8 bytes per
+    # edge-subset update, one u64 table entry read per update)
+    dom = max(kern.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    dom_units = units["C6"] if dom_name == "cycle_closure" else units["glasses"]
+    dom_units_per_launch = dom_units * args.steps / max(1, dom_n)
+    peak, peak_kind = measured_peaks()
+    achieved = 8.0 * dom_units_per_launch / (dom_ms / dom_n / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "avg_launch_ms": dom_ms / dom_n, "share_of_step": dom_ms / ms}
+
+    # end to end through the C-ABI with host buffers: load the CSR from host
+    # memory, count both queries, read the counts back, free the graph
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        gid2 = ctx.load_graph(g)
+        for name, q in qids.items():
+            ctx.count(gid2, q, trial_base + 50_000 + i, 1)
+        ctx.free_graph(gid2)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = g.row_ptr.nbytes + g.col.nbytes
+    e2e = {"value": units_step / e2e_s / 1e9 * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": 8 * len(qids) * 3, "ms_per_step": 1e3 * e2e_s}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": workload_name(), **WORKLOAD, "parallelism": f"replicas x{world}",
+                       "l2": "256 MB flush between steps, outside the events; working set > L2",
+                       "units_per_step": units_step, "units_by_query": units},
+            "colorings_per_s": colourings, "wall_s": wall,
+            "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kern.items()},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "e2e": e2e,
+            "counts_first_step": counts[0] if counts else None}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        u, s, nsrc = oracle_sample(g, 15.0)
+        line["cpu_baseline"] = {"value": u / s / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"C6 DP (single thread) restricted to {nsrc} random highest-vertex "
+                                          f"sources of the same graph and colouring: {u:.3g} updates in {s:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

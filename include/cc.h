@@ -1,0 +1,170 @@
+/*
+ * cc.h -- C-ABI of the GB300 colour-coding library for counting colourful
+ * matches of treewidth-2 query graphs (Chakaravarthy, Kapralov, Murali,
+ * Petrini, Que, Sabharwal, Schieber: "Subgraph Counting: Color Coding Beyond
+ * Trees", arXiv 1602.04478).
+ *
+ * The library keeps data graphs and per-query plans resident on one CUDA
+ * device and runs every step of the count in its own sm_103a kernels.  All
+ * pointers in this header are HOST pointers unless a name says "device".
+ * Every call is synchronous with respect to the host: results are in the
+ * caller's buffers when the call returns.  Calls on one context must not
+ * overlap (one host thread at a time per context).
+ *
+ * Problem (Section 2): for a query Q on k nodes and a data graph G, a match is
+ * an injective map pi: V_Q -> V_G with every query edge on a data edge.
+ * Given a colouring chi: V_G -> {0..k-1}, a match is colourful when its k
+ * images carry k distinct colours.  n_colorful(G, Q, chi) is the number of
+ * colourful matches; (k^k / k!) * E_chi[n_colorful] equals the number of
+ * matches, and dividing by aut(Q) counts subgraphs (Section 2, "Approximate
+ * subgraph counting via color coding").
+ *
+ * Colouring (the paper leaves the generator open): colour of vertex v
+ * (caller's id) in trial t under seed s is
+ *     hi64( mix(s ^ (G * (t + 1)) ^ mix(v)) * k ),
+ * where G = 0x9E3779B97F4A7C15, mix(x) is SplitMix64's output for state x
+ * (z = x + G; z = (z ^ z>>30) * 0xBF58476D1CE4E5B9;
+ *  z = (z ^ z>>27) * 0x94D049BB133111EB; z ^ z>>31) and hi64 the upper 64
+ * bits of the 128-bit product.  cc_set_colors replaces it with explicit
+ * colours.
+ *
+ * Error behaviour: every int-returning call returns CC_OK (0) or one of the
+ * negative CC_ERR_* codes below and leaves outputs it could not compute
+ * untouched unless stated.  cc_strerror gives a one-line message.
+ */
+#ifndef CC_H
+#define CC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CC_OK 0
+#define CC_ERR_INVALID_ARG (-1)  /* null pointer, out-of-range id or size     */
+#define CC_ERR_BAD_GRAPH (-2)    /* CSR not symmetric, self-loop, duplicate    */
+#define CC_ERR_NOT_TW2 (-3)      /* query has no block decomposition (tw > 2)  */
+#define CC_ERR_K_RANGE (-4)      /* k outside [2, 12]                          */
+#define CC_ERR_OOM (-5)          /* device memory would exceed the budget      */
+#define CC_ERR_OVERFLOW (-6)     /* a count exceeded 2^64-1 (never wrapped)    */
+#define CC_ERR_TIMEOUT (-7)      /* a bounded device wait gave up              */
+#define CC_ERR_CUDA (-8)         /* a CUDA runtime call failed                 */
+#define CC_ERR_UNSUPPORTED (-9)  /* the query needs a block kind not built    */
+#define CC_ERR_NOT_CONNECTED (-10) /* the query graph is not connected         */
+
+#define CC_MAX_K 12
+
+typedef struct cc_ctx cc_ctx;
+
+/* Device-memory allocator hooks.  alloc returns a device pointer of at least
+ * `bytes` bytes (16-byte aligned) or NULL; free releases it.  Without hooks
+ * the library uses cudaMalloc / cudaFree. */
+typedef void *(*cc_alloc_fn)(size_t bytes, void *user);
+typedef void (*cc_free_fn)(void *ptr, size_t bytes, void *user);
+
+/* Create a context on CUDA device `device` that issues all work on
+ * `cuda_stream` (a cudaStream_t; NULL means the legacy default stream).
+ * The context owns every device buffer it allocates. */
+int cc_create(cc_ctx **out, int device, void *cuda_stream);
+void cc_destroy(cc_ctx *ctx);
+int cc_set_allocator(cc_ctx *ctx, cc_alloc_fn alloc, cc_free_fn free_fn, void *user);
+/* Upper bound on the device bytes the context may hold (0 = no limit).
+ * A count whose tables would exceed it fails with CC_ERR_OOM before any
+ * launch. */
+int cc_set_memory_budget(cc_ctx *ctx, size_t bytes);
+
+/* Copy a data graph to the device.  row_ptr[n+1] (int64) and col[nnz]
+ * (int32, caller's vertex ids) describe a symmetric simple graph: each
+ * undirected edge appears in both rows, no self-loops, no duplicates.
+ * Anything else fails with CC_ERR_BAD_GRAPH (no silent repair).  The caller
+ * keeps ownership of its arrays.  The library orders vertices by
+ * (degree, id) ascending -- the degree order of Section 5.1 -- and stores the
+ * graph relabelled by that rank. */
+int cc_load_csr(cc_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                int64_t nnz, int32_t *graph_id);
+int cc_free_graph(cc_ctx *ctx, int32_t graph_id);
+int cc_graph_info(cc_ctx *ctx, int32_t graph_id, int64_t *n, int64_t *nnz, int64_t *max_degree);
+
+/* Register a query: k nodes (2..12) and n_edges edges as pairs
+ * edges[2i], edges[2i+1] in 0..k-1.  The query must be simple and
+ * connected.  The library decomposes it into blocks (Section 4.1: leaf
+ * edges and induced cycles with at most two boundary nodes, contracted by
+ * Cases 1-3) and computes aut(Q) by enumeration.  CC_ERR_NOT_TW2 when no
+ * decomposition exists (Lemma 4.1), CC_ERR_UNSUPPORTED when every
+ * decomposition needs a non-root cycle block longer than a triangle or a
+ * root cycle longer than 8. */
+int cc_set_query(cc_ctx *ctx, int k, int n_edges, const int32_t *edges, int32_t *query_id);
+
+/* Replace the query's decomposition by an explicit contraction order.
+ * block_seq is a list of records, one per contracted block, in order:
+ *   0, a, b          leaf edge (a, b) whose node b has degree one
+ *   L, a0, .., aL-1  induced cycle of length L >= 3 in cyclic order
+ * The final block (root cycle or single node) is implied.  Each record
+ * must name a block of the partly contracted query at that point, else
+ * CC_ERR_INVALID_ARG.  Every valid order gives the same counts (Section 5.2);
+ * the order only changes the work. */
+int cc_set_decomposition(cc_ctx *ctx, int32_t query_id, const int32_t *block_seq, int len);
+
+/* Host-only (no context, no device): the decomposition the library would
+ * use for a query, with an optional explicit order (block_seq as for
+ * cc_set_decomposition, NULL/0 for the default plan).  Writes one record per
+ * block in contraction order -- kind (0 leaf, 1 triangle, 2 root cycle of
+ * length >= 4, 3 root node, 4 non-root cycle of length >= 4), L, L nodes,
+ * number of boundary nodes, the boundary nodes, the number of children, the
+ * children's block indices -- into out[cap] and aut(Q) into *aut.  Returns the
+ * number of int32 words (more than cap means truncated) or a CC_ERR_ code.
+ * A plan with a kind-4 block is returned too; cc_set_query refuses it with
+ * CC_ERR_UNSUPPORTED. */
+int cc_plan_inspect(int k, int n_edges, const int32_t *edges, const int32_t *block_seq, int seq_len,
+                    int32_t *out, int cap, int64_t *aut);
+
+/* Query facts: k, aut(Q), number of blocks, longest cycle block. */
+int cc_query_info(cc_ctx *ctx, int32_t query_id, int *k, int64_t *aut, int *n_blocks,
+                  int *longest_cycle);
+
+/* Colouring seed for the hash colouring above (default 1). */
+int cc_set_coloring_seed(cc_ctx *ctx, uint64_t seed);
+/* Explicit colours for graph_id: colors[t * n + v] in 0..k-1 for T trials,
+ * v the caller's vertex id.  Counts then use trial t's row for trial t
+ * (t < T).  cc_clear_colors returns to the hash colouring. */
+int cc_set_colors(cc_ctx *ctx, int32_t graph_id, const uint8_t *colors, int T);
+int cc_clear_colors(cc_ctx *ctx, int32_t graph_id);
+
+/* Plain form: count colourful matches of query_id in graph_id for trials
+ * first_trial .. first_trial+T-1, one colouring per pass.
+ * colorful[T]: colourful match counts (uint64).  estimate[T] (nullable):
+ * colorful * k^k / k! / aut(Q), the subgraph-count estimate of that trial.
+ * aut (nullable): aut(Q).  On CC_ERR_OVERFLOW the overflowing trials'
+ * colorful entries are UINT64_MAX and the other trials are still filled. */
+int cc_count(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int first_trial, int T,
+             uint64_t *colorful, double *estimate, double *aut);
+
+/* One trial, and the count split by vertex: for a root cycle block the
+ * colourful matches whose highest root-cycle vertex (degree order) is v;
+ * for a root that is a single node, the matches mapping that node to v.
+ * per_vertex[n] is indexed by the caller's vertex ids and sums to *total. */
+int cc_count_per_vertex(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int trial,
+                        uint64_t *per_vertex, uint64_t *total);
+
+/* Structural work of one colouring of query_id on graph_id in edge-subset
+ * updates (independent of the colouring; see the design notes): the sum,
+ * over every table-building step, of the data edges it scans times the
+ * signature slots of the rows it extends. */
+int cc_work_units(cc_ctx *ctx, int32_t graph_id, int32_t query_id, double *units);
+
+/* Kernel timing: when enabled, the library brackets each kernel launch with
+ * CUDA events on its stream and accumulates the time per kernel name.
+ * cc_get_timing copies up to `cap` names (NUL-terminated, 48 bytes each),
+ * accumulated milliseconds and launch counts; returns the number of names. */
+int cc_set_timing(cc_ctx *ctx, int enable);
+int cc_get_timing(cc_ctx *ctx, char *names, double *ms, int64_t *launches, int cap);
+int cc_reset_timing(cc_ctx *ctx);
+
+const char *cc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CC_H */

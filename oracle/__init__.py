@@ -69,7 +69,10 @@ def _load():
         lib.or_automorphisms.restype = ctypes.c_int64
         lib.or_dp_count.argtypes = [ctypes.c_int64, I64P, I32P, ctypes.c_int, ctypes.c_int, I32P, U8P,
                                     ctypes.c_int, I64P, I32P, ctypes.c_int, U8P, U64P, U64P,
-                                    ctypes.POINTER(ctypes.c_int)]
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        lib.or_cycle_units.argtypes = [ctypes.c_int64, I64P, I32P, ctypes.c_int, ctypes.c_int, U8P,
+                                       ctypes.POINTER(ctypes.c_double)]
+        lib.or_cycle_units.restype = ctypes.c_double
         lib.or_decompose.argtypes = [ctypes.c_int, ctypes.c_int, I32P, I32P, ctypes.c_int, I32P,
                                      ctypes.c_int, I32P, ctypes.c_int, I32P]
         for f in (lib.or_brute_colorful, lib.or_brute_matches, lib.or_dp_count, lib.or_decompose):
@@ -143,7 +146,8 @@ class NotTreewidth2(ValueError):
     pass
 
 
-def dp_count(g, k, edges, col, order="degree", choice=None, root_filter=None, per_source=False):
+def dp_count(g, k, edges, col, order="degree", choice=None, root_filter=None, per_source=False,
+             timing=None):
     """Colourful matches by the paper's dynamic program.
 
     order: "degree" (DB, Section 5.1 order), "id" (DB with ids as the order),
@@ -166,12 +170,15 @@ def dp_count(g, k, edges, col, order="degree", choice=None, root_filter=None, pe
     ps = np.zeros(2 * max(g.n, 1), dtype=np.uint64) if per_source else None
     out = np.zeros(2, dtype=np.uint64)
     ovf = ctypes.c_int(0)
+    secs = ctypes.c_double(0)
     rc = _load().or_dp_count(g.n, _p(rp, ctypes.c_int64), _p(cl, ctypes.c_int32), k, ne,
                              _p(e, ctypes.c_int32), _p(c, ctypes.c_uint8), kind,
                              _p(rank, ctypes.c_int64), _p(ch, ctypes.c_int32),
                              len(choice) if choice is not None else 0,
                              _p(filt, ctypes.c_uint8), _p(ps, ctypes.c_uint64),
-                             _p(out, ctypes.c_uint64), ctypes.byref(ovf))
+                             _p(out, ctypes.c_uint64), ctypes.byref(ovf), ctypes.byref(secs))
+    if timing is not None:
+        timing["dp_seconds"] = secs.value
     if rc == -2:
         raise NotTreewidth2("query has no decomposition into blocks (treewidth above 2)")
     if rc != 0:
@@ -234,3 +241,13 @@ def all_plans(k, edges, limit=10000):
 
     rec([])
     return plans
+
+
+def cycle_units(g, L, k, source_filter=None, per_source=False):
+    """Structural DB work (edge-subset updates) of a plain root L-cycle."""
+    rp, cl = _graph_arrays(g)
+    filt = np.ascontiguousarray(source_filter, dtype=np.uint8) if source_filter is not None else None
+    ps = np.zeros(max(g.n, 1), dtype=np.float64) if per_source else None
+    tot = _load().or_cycle_units(g.n, _p(rp, ctypes.c_int64), _p(cl, ctypes.c_int32), L, k,
+                                 _p(filt, ctypes.c_uint8), _p(ps, ctypes.c_double))
+    return (tot, ps[:g.n]) if per_source else tot

@@ -35,6 +35,7 @@
 // Counts are accumulated in unsigned 128-bit integers; any table entry or the
 // final count above 2^64-1 sets the overflow flag.
 #include <algorithm>
+#include <chrono>
 #include <cstdint>
 #include <cstring>
 #include <functional>
@@ -809,7 +810,7 @@ extern "C" int or_dp_count(int64_t n, const int64_t *row_ptr, const int32_t *col
                            const int32_t *qedges, const uint8_t *colors, int order_kind,
                            const int64_t *rank_in, const int32_t *choice, int n_choice,
                            const uint8_t *root_filter, uint64_t *per_source128, uint64_t *out128,
-                           int *overflow) {
+                           int *overflow, double *dp_seconds) {
   DGraph g;
   QGraph q;
   if (!load_query(q, k, ne, qedges)) return -1;
@@ -836,7 +837,10 @@ extern "C" int or_dp_count(int64_t n, const int64_t *row_ptr, const int32_t *col
     ps.assign((size_t)n, 0);
     C.per_source = &ps;
   }
+  auto t0 = std::chrono::steady_clock::now();
   u128 r = run_dp(C, D, per_source128 ? &ps : nullptr);
+  if (dp_seconds)
+    *dp_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   put128(r, out128);
   if (per_source128)
     for (int64_t v = 0; v < n; v++) put128(ps[v], per_source128 + 2 * v);
@@ -873,4 +877,54 @@ extern "C" int or_decompose(int k, int ne, const int32_t *qedges, const int32_t 
   }
   *root_out = D.root;
   return (int)D.blocks.size();
+}
+
+// Structural work of the DB procedure on a plain (unannotated) root cycle of
+// length L with k colours, in edge-subset updates: for each source u and each
+// half (depth floor(L/2) and ceil(L/2)), level sets L_0 = {u},
+// L_{j+1} = lower-than-u neighbours of L_j; extending level j scans
+// sum_{v in L_j} |{w in N(v): w < u}| edges, each against C(k-2, j-1) signature
+// slots (level 0: one slot).  One highest-node choice (rotations of a plain
+// cycle give equal counts).  A source with fewer than two lower neighbours
+// closes no cycle and does no work.  Independent of the colouring.
+// source_filter (nullable): only these sources; per_source (nullable): units by u.
+extern "C" double or_cycle_units(int64_t n, const int64_t *row_ptr, const int32_t *col, int L, int k,
+                                 const uint8_t *source_filter, double *per_source) {
+  DGraph g;
+  load_graph(g, n, row_ptr, col);
+  std::vector<int64_t> rank = degree_rank(g);
+  auto binom = [](int a, int b) -> double {
+    if (b < 0 || b > a) return 0.0;
+    double r = 1;
+    for (int i = 1; i <= b; i++) r = r * (a - b + i) / i;
+    return r;
+  };
+  double total = 0;
+  std::vector<int64_t> mark((size_t)n, -1);
+  for (int64_t u = 0; u < n; u++) {
+    if (source_filter && !source_filter[u]) continue;
+    int lower = 0;
+    for (int32_t w : g.adj[u]) lower += rank[w] < rank[u];
+    if (lower < 2) continue;
+    double mine = 0;
+    for (int half = 0; half < 2; half++) {
+      int depth = half == 0 ? L / 2 : L - L / 2;
+      std::vector<int32_t> level{(int32_t)u};
+      for (int j = 0; j < depth; j++) {
+        double slots = j == 0 ? 1.0 : binom(k - 2, j - 1);
+        std::vector<int32_t> next;
+        int64_t tag = (int64_t)u * 16 + half * 8 + j;
+        for (int32_t v : level)
+          for (int32_t w : g.adj[v]) {
+            if (rank[w] >= rank[u]) continue;
+            mine += slots;
+            if (mark[w] != tag) { mark[w] = tag; next.push_back(w); }
+          }
+        level.swap(next);
+      }
+    }
+    total += mine;
+    if (per_source) per_source[u] = mine;
+  }
+  return total;
 }

@@ -1,0 +1,632 @@
+// C-ABI entry points and the plan executor.
+//
+// The executor walks the decomposition tree bottom-up (Section 4.2, figure
+// "Overall Algorithm"): every non-root block gets a projection table --
+// unary [n][R] for one boundary node, edge-keyed [nnz][R] for two -- built
+// from its children's tables, and the root block is reduced to the count of
+// colourful matches.  Tables of a block are freed once its parent has run.
+// The estimate is colorful * k^k / k! / aut(Q) (Section 2).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cc_kernels.h"
+
+struct cc_ctx {
+  cc::Ctx c;
+};
+
+namespace cc {
+
+void *dev_alloc(Ctx &c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (c.budget && c.in_use + bytes > c.budget) return nullptr;
+  void *p = nullptr;
+  if (c.alloc) {
+    p = c.alloc(bytes, c.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c.in_use += bytes;
+  return p;
+}
+
+void dev_free(Ctx &c, void *p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  if (c.free_fn) c.free_fn(p, bytes, c.alloc_user);
+  else cudaFree(p);
+  c.in_use -= std::min(c.in_use, bytes);
+}
+
+int ensure_scratch(Ctx &c, size_t bytes) {
+  if (c.scratch_bytes >= bytes) return CC_OK;
+  if (c.scratch) {
+    cudaStreamSynchronize(c.stream);
+    dev_free(c, c.scratch, c.scratch_bytes);
+  }
+  c.scratch = nullptr;
+  c.scratch_bytes = 0;
+  c.scratch = dev_alloc(c, bytes);
+  if (!c.scratch) return CC_ERR_OOM;
+  c.scratch_bytes = bytes;
+  c.scratch_dirty = true;
+  return CC_OK;
+}
+
+void timing_begin(Ctx &c, const char *name) {
+  if (!c.timing) return;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, c.stream);
+  c.pending.push_back({name, {a, b}});
+}
+
+void timing_end(Ctx &c) {
+  if (!c.timing || c.pending.empty()) return;
+  cudaEventRecord(c.pending.back().second.second, c.stream);
+}
+
+void timing_flush(Ctx &c) {
+  if (c.pending.empty()) return;
+  cudaStreamSynchronize(c.stream);
+  for (auto &p : c.pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+    auto &t = c.times[p.first];
+    t.first += ms;
+    t.second += 1;
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  c.pending.clear();
+}
+
+namespace {
+
+struct Table {
+  u64 *p = nullptr;
+  size_t bytes = 0;
+  int arity = 0;  // 1 unary, 2 edge-keyed
+  int s = 0, R = 0;
+};
+
+TabU tab_u(const std::vector<Table> &T, int idx) {
+  TabU t;
+  if (idx < 0) return t;
+  t.p = T[idx].p;
+  t.s = T[idx].s;
+  t.R = T[idx].R;
+  return t;
+}
+TabE tab_e(const std::vector<Table> &T, int idx, bool use_rev) {
+  TabE t;
+  if (idx < 0) return t;
+  t.p = T[idx].p;
+  t.s = T[idx].s;
+  t.R = T[idx].R;
+  t.use_rev = use_rev;
+  return t;
+}
+
+size_t table_bytes(const Plan &p, const Stage &st, const DevGraph &g, int *R_out, int *arity) {
+  int k = p.k;
+  if (st.kind == ST_LEAF || (st.kind == ST_TRI && st.nb == 1)) {
+    *arity = 1;
+    *R_out = (int)binom(k - 1, st.s - 1);
+    return (size_t)g.n * *R_out * 8;
+  }
+  if (st.kind == ST_TRI && st.nb == 2) {
+    *arity = 2;
+    *R_out = (int)binom(k - 2, st.s - 2);
+    return (size_t)std::max<int64_t>(g.nnz, 1) * *R_out * 8;
+  }
+  *arity = 0;
+  *R_out = 0;
+  return 0;
+}
+
+int check(cudaError_t e) { return e == cudaSuccess ? CC_OK : CC_ERR_CUDA; }
+
+// Bytes the tables of one colouring pass hold at their peak (all live at once).
+size_t plan_table_bytes(const Plan &p, const DevGraph &g) {
+  size_t total = 0;
+  for (auto &st : p.stages) {
+    int R, ar;
+    total += table_bytes(p, st, g, &R, &ar);
+  }
+  return total;
+}
+
+// One colouring pass of the plan.  d_per_vertex (rank order, nullable)
+// receives the root's split by vertex.
+int run_plan(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, u64 *count, bool *overflow,
+             u64 *d_per_vertex, double *units = nullptr) {
+  const int k = p.k;
+  if (c.budget && c.in_use + plan_table_bytes(p, g) + (size_t)g.n > c.budget) return CC_ERR_OOM;
+  uint8_t *d_col = (uint8_t *)dev_alloc(c, (size_t)g.n);
+  if (!d_col) return CC_ERR_OOM;
+  int *d_counter = (int *)dev_alloc(c, 256);
+  std::vector<Table> T(p.stages.size());
+  int rc = CC_OK;
+  auto release = [&]() {
+    cudaStreamSynchronize(c.stream);
+    for (auto &t : T) dev_free(c, t.p, t.bytes);
+    dev_free(c, d_col, (size_t)g.n);
+    dev_free(c, d_counter, 256);
+  };
+  if (!d_counter) { release(); return CC_ERR_OOM; }
+  if ((rc = check(cudaMemsetAsync(c.d_status, 0, 8 * sizeof(u64), c.stream))) != CC_OK) { release(); return rc; }
+  double host_units = 0.0;
+  if ((rc = colors_fill(c, g, k, trial, d_col)) != CC_OK) { release(); return rc; }
+  if (d_per_vertex && (rc = check(cudaMemsetAsync(d_per_vertex, 0, (size_t)g.n * 8, c.stream))) != CC_OK) {
+    release();
+    return rc;
+  }
+  Lut lut{c.lut_rank, c.lut_unrank};
+  GraphView gv = view_of(g);
+  for (size_t i = 0; i < p.stages.size() && rc == CC_OK; i++) {
+    const Stage &st = p.stages[i];
+    bool is_root = i + 1 == p.stages.size();
+    int R = 0, ar = 0;
+    size_t bytes = table_bytes(p, st, g, &R, &ar);
+    if (bytes) {
+      T[i].p = (u64 *)dev_alloc(c, bytes);
+      if (!T[i].p) { rc = CC_ERR_OOM; break; }
+      T[i].bytes = bytes;
+      T[i].arity = ar;
+      T[i].s = st.s;
+      T[i].R = R;
+      if ((rc = check(cudaMemsetAsync(T[i].p, 0, bytes, c.stream))) != CC_OK) break;
+    }
+    if (st.kind == ST_LEAF) {
+      LeafArgs a;
+      a.g = gv;
+      a.colors = d_col;
+      a.k = k;
+      a.lut = lut;
+      a.A = tab_u(T, st.node_child[0]);
+      a.B = tab_u(T, st.node_child[1]);
+      a.E = tab_e(T, st.edge_child[0], !st.edge_fwd[0]);
+      int sE = a.E.p ? a.E.s : 2, sB = a.B.p ? a.B.s : 1, sA = a.A.p ? a.A.s : 1;
+      a.sY = sE + sB - 1;
+      a.RY = (int)binom(k - 1, a.sY - 1);
+      a.out = T[i].p;
+      a.s_out = st.s;
+      a.R_out = R;
+      a.status = c.d_status;
+      if (sA + a.sY - 1 != st.s) { rc = CC_ERR_INVALID_ARG; break; }
+      // every directed edge joins one edge row with one row of the leaf's block
+      host_units += (double)g.nnz * (a.E.p ? a.E.R : 1) * (a.B.p ? a.B.R : 1);
+      rc = launch_leaf(c, a);
+    } else if (st.kind == ST_TRI) {
+      TriArgs a;
+      a.g = gv;
+      a.colors = d_col;
+      a.k = k;
+      a.lut = lut;
+      for (int j = 0; j < 3; j++) {
+        a.N[j] = tab_u(T, st.node_child[j]);
+        a.E[j] = tab_e(T, st.edge_child[j], !st.edge_fwd[j]);
+      }
+      a.nb = st.nb;
+      for (int b = 0; b < st.nb; b++)
+        for (int j = 0; j < 3; j++)
+          if (st.nodes[j] == st.bd[b]) a.bd[b] = j;
+      a.s_out = st.s;
+      a.R_out = R;
+      a.out = T[i].p;
+      a.per_vertex = is_root ? d_per_vertex : nullptr;
+      a.status = c.d_status;
+      a.work_counter = d_counter;
+      a.count_units = units != nullptr;
+      rc = launch_triangle(c, a);
+    } else if (st.kind == ST_CYCLE_ROOT) {
+      CycleArgs a;
+      a.g = gv;
+      a.colors = d_col;
+      a.k = k;
+      a.lut = lut;
+      a.L = st.L;
+      bool plain = true;
+      for (int j = 0; j < st.L; j++) {
+        a.N[j] = tab_u(T, st.node_child[j]);
+        a.Efw[j] = tab_e(T, st.edge_child[j], !st.edge_fwd[j]);
+        a.Ebw[j] = tab_e(T, st.edge_child[j], st.edge_fwd[j]);
+        plain = plain && st.node_child[j] < 0 && st.edge_child[j] < 0;
+      }
+      if (plain) {
+        a.n_h = 1;
+        a.hs[0] = 0;
+        a.multiplier = st.L;
+      } else {
+        a.n_h = st.L;
+        for (int h = 0; h < st.L; h++) a.hs[h] = h;
+        a.multiplier = 1;
+      }
+      a.per_vertex = d_per_vertex;
+      a.status = c.d_status;
+      a.count_units = units != nullptr;
+      rc = launch_cycle(c, a);
+      if (rc != CC_OK) c.scratch_dirty = true;
+    } else if (st.kind == ST_ROOT_NODE) {
+      const Table &ct = T[st.node_child[0]];
+      if (ct.R != 1) { rc = CC_ERR_INVALID_ARG; break; }
+      rc = launch_root_sum(c, gv, ct.p, d_per_vertex, c.d_status);
+    } else {
+      rc = CC_ERR_UNSUPPORTED;
+    }
+    // children's tables are no longer needed
+    if (rc == CC_OK) {
+      int nchild = st.kind == ST_ROOT_NODE ? 1 : st.L;
+      std::vector<int> kids;
+      for (int j = 0; j < nchild; j++) {
+        if (st.node_child[j] >= 0) kids.push_back(st.node_child[j]);
+        if (st.edge_child[j] >= 0) kids.push_back(st.edge_child[j]);
+      }
+      if (!kids.empty()) {
+        cudaStreamSynchronize(c.stream);
+        for (int kid : kids) {
+          dev_free(c, T[kid].p, T[kid].bytes);
+          T[kid].p = nullptr;
+          T[kid].bytes = 0;
+        }
+      }
+    }
+  }
+  u64 status[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (rc == CC_OK) {
+    rc = check(cudaMemcpyAsync(status, c.d_status, sizeof(status), cudaMemcpyDeviceToHost, c.stream));
+    if (rc == CC_OK) rc = check(cudaStreamSynchronize(c.stream));
+  }
+  timing_flush(c);
+  release();
+  if (rc != CC_OK) return rc;
+  if (status[ST_TIMEOUT] & 1ull) return CC_ERR_TIMEOUT;
+  if (status[ST_TIMEOUT] & 2ull) return CC_ERR_UNSUPPORTED;
+  *count = status[ST_COUNT];
+  *overflow = status[ST_OVERFLOW] != 0;
+  if (units) *units = host_units + (double)status[ST_UNITS];
+  return CC_OK;
+}
+
+}  // namespace
+}  // namespace cc
+
+using namespace cc;
+
+extern "C" {
+
+const char *cc_strerror(int code) {
+  switch (code) {
+    case CC_OK: return "ok";
+    case CC_ERR_INVALID_ARG: return "invalid argument";
+    case CC_ERR_BAD_GRAPH: return "graph is not a symmetric simple CSR (self-loop, duplicate or missing reverse edge)";
+    case CC_ERR_NOT_TW2: return "query has no block decomposition: treewidth above 2";
+    case CC_ERR_K_RANGE: return "query size k outside [2, 12]";
+    case CC_ERR_OOM: return "device memory budget exceeded";
+    case CC_ERR_OVERFLOW: return "a count exceeded 2^64-1";
+    case CC_ERR_TIMEOUT: return "a bounded device wait gave up";
+    case CC_ERR_CUDA: return "CUDA runtime error";
+    case CC_ERR_UNSUPPORTED: return "query needs a block kind without a kernel (non-root cycle longer than 3, or root cycle longer than 8)";
+    case CC_ERR_NOT_CONNECTED: return "query graph is not connected";
+    default: return "unknown error";
+  }
+}
+
+int cc_create(cc_ctx **out, int device, void *cuda_stream) {
+  if (!out) return CC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return CC_ERR_CUDA;
+  cc_ctx *x = new cc_ctx();
+  x->c.device = device;
+  x->c.stream = (cudaStream_t)cuda_stream;
+  x->c.d_status = (u64 *)dev_alloc(x->c, 64);
+  int rc = x->c.d_status ? luts_init(x->c) : CC_ERR_OOM;
+  if (rc != CC_OK) {
+    cc_destroy(x);
+    return rc;
+  }
+  *out = x;
+  return CC_OK;
+}
+
+void cc_destroy(cc_ctx *ctx) {
+  if (!ctx) return;
+  Ctx &c = ctx->c;
+  cudaSetDevice(c.device);
+  cudaStreamSynchronize(c.stream);
+  for (auto &g : c.graphs) graph_free(c, g.second);
+  dev_free(c, c.scratch, c.scratch_bytes);
+  dev_free(c, c.lut_rank, 4096 * 2);
+  dev_free(c, c.lut_unrank, 13 * kUnrankStride * 2);
+  dev_free(c, c.d_status, 64);
+  delete ctx;
+}
+
+int cc_set_allocator(cc_ctx *ctx, cc_alloc_fn alloc, cc_free_fn free_fn, void *user) {
+  if (!ctx || (!alloc) != (!free_fn)) return CC_ERR_INVALID_ARG;
+  Ctx &c = ctx->c;
+  if (!c.graphs.empty() || c.scratch) return CC_ERR_INVALID_ARG;  // set before any allocation
+  // the context's own small buffers move to the new allocator
+  cudaStreamSynchronize(c.stream);
+  dev_free(c, c.lut_rank, 4096 * 2);
+  dev_free(c, c.lut_unrank, 13 * kUnrankStride * 2);
+  dev_free(c, c.d_status, 64);
+  c.alloc = alloc;
+  c.free_fn = free_fn;
+  c.alloc_user = user;
+  c.d_status = (u64 *)dev_alloc(c, 64);
+  if (!c.d_status) return CC_ERR_OOM;
+  return luts_init(c);
+}
+
+int cc_set_memory_budget(cc_ctx *ctx, size_t bytes) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  ctx->c.budget = bytes;
+  return CC_OK;
+}
+
+int cc_load_csr(cc_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col, int64_t nnz,
+                int32_t *graph_id) {
+  if (!ctx || !graph_id) return CC_ERR_INVALID_ARG;
+  Ctx &c = ctx->c;
+  cudaSetDevice(c.device);
+  DevGraph g;
+  int rc = graph_load(c, n, row_ptr, col, nnz, g);
+  if (rc != CC_OK) return rc;
+  int id = c.next_graph++;
+  c.graphs[id] = g;
+  *graph_id = id;
+  return CC_OK;
+}
+
+int cc_free_graph(cc_ctx *ctx, int32_t graph_id) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  auto it = ctx->c.graphs.find(graph_id);
+  if (it == ctx->c.graphs.end()) return CC_ERR_INVALID_ARG;
+  cudaStreamSynchronize(ctx->c.stream);
+  graph_free(ctx->c, it->second);
+  ctx->c.graphs.erase(it);
+  return CC_OK;
+}
+
+int cc_graph_info(cc_ctx *ctx, int32_t graph_id, int64_t *n, int64_t *nnz, int64_t *max_degree) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  auto it = ctx->c.graphs.find(graph_id);
+  if (it == ctx->c.graphs.end()) return CC_ERR_INVALID_ARG;
+  if (n) *n = it->second.n;
+  if (nnz) *nnz = it->second.nnz;
+  if (max_degree) *max_degree = it->second.max_deg;
+  return CC_OK;
+}
+
+int cc_set_query(cc_ctx *ctx, int k, int n_edges, const int32_t *edges, int32_t *query_id) {
+  if (!ctx || !query_id || n_edges < 0 || (n_edges > 0 && !edges)) return CC_ERR_INVALID_ARG;
+  std::vector<std::pair<int, int>> e;
+  for (int i = 0; i < n_edges; i++) e.push_back({edges[2 * i], edges[2 * i + 1]});
+  Plan p;
+  int rc = plan_query(k, e, p);
+  if (rc != CC_OK) return rc;
+  int id = ctx->c.next_query++;
+  ctx->c.plans[id] = p;
+  *query_id = id;
+  return CC_OK;
+}
+
+int cc_set_decomposition(cc_ctx *ctx, int32_t query_id, const int32_t *block_seq, int len) {
+  if (!ctx || len < 0 || (len > 0 && !block_seq)) return CC_ERR_INVALID_ARG;
+  auto it = ctx->c.plans.find(query_id);
+  if (it == ctx->c.plans.end()) return CC_ERR_INVALID_ARG;
+  std::vector<int> seq(block_seq, block_seq + len);
+  Plan p;
+  int rc = plan_explicit(it->second.k, it->second.edges, seq, p);
+  if (rc != CC_OK) return rc;
+  it->second = p;
+  for (auto &g : ctx->c.graphs) g.second.work_cache.erase(query_id);
+  return CC_OK;
+}
+
+int cc_plan_inspect(int k, int n_edges, const int32_t *edges, const int32_t *block_seq, int seq_len, int32_t *out,
+                    int cap, int64_t *aut) {
+  if (n_edges < 0 || (n_edges > 0 && !edges) || seq_len < 0 || (seq_len > 0 && !block_seq) || cap < 0 ||
+      (cap > 0 && !out))
+    return CC_ERR_INVALID_ARG;
+  std::vector<std::pair<int, int>> e;
+  for (int i = 0; i < n_edges; i++) e.push_back({edges[2 * i], edges[2 * i + 1]});
+  Plan p;
+  int rc = seq_len > 0 ? plan_explicit(k, e, std::vector<int>(block_seq, block_seq + seq_len), p)
+                       : plan_query(k, e, p);
+  if (rc != CC_OK && rc != CC_ERR_UNSUPPORTED) return rc;
+  if (p.stages.empty()) return rc;
+  int w = 0;
+  auto put = [&](int32_t x) {
+    if (w < cap) out[w] = x;
+    w++;
+  };
+  for (auto &st : p.stages) {
+    put(st.kind);
+    int L = st.kind == ST_ROOT_NODE ? 1 : st.L;
+    put(L);
+    for (int i = 0; i < L; i++) put(st.nodes[i]);
+    put(st.nb);
+    for (int i = 0; i < st.nb; i++) put(st.bd[i]);
+    std::vector<int> kids;
+    int ne = st.kind == ST_LEAF ? 1 : (st.kind == ST_ROOT_NODE ? 0 : L);
+    for (int i = 0; i < L; i++)
+      if (st.node_child[i] >= 0) kids.push_back(st.node_child[i]);
+    for (int i = 0; i < ne; i++)
+      if (st.edge_child[i] >= 0) kids.push_back(st.edge_child[i]);
+    put((int32_t)kids.size());
+    for (int x : kids) put(x);
+  }
+  if (aut) *aut = p.aut;
+  return w;
+}
+
+int cc_query_info(cc_ctx *ctx, int32_t query_id, int *k, int64_t *aut, int *n_blocks, int *longest_cycle) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  auto it = ctx->c.plans.find(query_id);
+  if (it == ctx->c.plans.end()) return CC_ERR_INVALID_ARG;
+  if (k) *k = it->second.k;
+  if (aut) *aut = it->second.aut;
+  if (n_blocks) *n_blocks = (int)it->second.stages.size();
+  if (longest_cycle) *longest_cycle = it->second.longest_cycle;
+  return CC_OK;
+}
+
+int cc_set_coloring_seed(cc_ctx *ctx, uint64_t seed) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  ctx->c.seed = seed;
+  return CC_OK;
+}
+
+int cc_set_colors(cc_ctx *ctx, int32_t graph_id, const uint8_t *colors, int T) {
+  if (!ctx || !colors || T <= 0) return CC_ERR_INVALID_ARG;
+  auto it = ctx->c.graphs.find(graph_id);
+  if (it == ctx->c.graphs.end()) return CC_ERR_INVALID_ARG;
+  int mx = 0;
+  for (int64_t i = 0; i < (int64_t)T * it->second.n; i++) mx = std::max<int>(mx, colors[i]);
+  if (mx >= CC_MAX_K) return CC_ERR_INVALID_ARG;
+  int rc = colors_set(ctx->c, it->second, colors, T);
+  if (rc == CC_OK) it->second.colors_max = mx;
+  return rc;
+}
+
+int cc_clear_colors(cc_ctx *ctx, int32_t graph_id) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  auto it = ctx->c.graphs.find(graph_id);
+  if (it == ctx->c.graphs.end()) return CC_ERR_INVALID_ARG;
+  return colors_set(ctx->c, it->second, nullptr, 0);
+}
+
+static int lookup(cc_ctx *ctx, int32_t graph_id, int32_t query_id, DevGraph **g, Plan **p) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  auto gi = ctx->c.graphs.find(graph_id);
+  auto pi = ctx->c.plans.find(query_id);
+  if (gi == ctx->c.graphs.end() || pi == ctx->c.plans.end()) return CC_ERR_INVALID_ARG;
+  *g = &gi->second;
+  *p = &pi->second;
+  if (!(*p)->supported) return CC_ERR_UNSUPPORTED;
+  // explicit colours must lie in 0..k-1 for this query
+  if (gi->second.colors && gi->second.colors_max >= (*p)->k) return CC_ERR_INVALID_ARG;
+  return CC_OK;
+}
+
+int cc_count(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int first_trial, int T, uint64_t *colorful,
+             double *estimate, double *aut) {
+  DevGraph *g;
+  Plan *p;
+  int rc = lookup(ctx, graph_id, query_id, &g, &p);
+  if (rc != CC_OK) return rc;
+  if (T <= 0 || first_trial < 0 || !colorful) return CC_ERR_INVALID_ARG;
+  Ctx &c = ctx->c;
+  cudaSetDevice(c.device);
+  double scale = 1.0;
+  for (int i = 0; i < p->k; i++) scale *= (double)p->k / (double)(i + 1);  // k^k / k!
+  int final_rc = CC_OK;
+  for (int t = 0; t < T; t++) {
+    u64 cnt = 0;
+    bool ovf = false;
+    rc = run_plan(c, *g, *p, (int64_t)first_trial + t, &cnt, &ovf, nullptr);
+    if (rc != CC_OK) return rc;
+    if (ovf) {
+      colorful[t] = UINT64_MAX;
+      final_rc = CC_ERR_OVERFLOW;
+    } else {
+      colorful[t] = cnt;
+    }
+    if (estimate) estimate[t] = ovf ? INFINITY : (double)cnt * scale / (double)p->aut;
+  }
+  if (aut) *aut = (double)p->aut;
+  return final_rc;
+}
+
+int cc_count_per_vertex(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int trial, uint64_t *per_vertex,
+                        uint64_t *total) {
+  DevGraph *g;
+  Plan *p;
+  int rc = lookup(ctx, graph_id, query_id, &g, &p);
+  if (rc != CC_OK) return rc;
+  if (!per_vertex || trial < 0) return CC_ERR_INVALID_ARG;
+  Ctx &c = ctx->c;
+  cudaSetDevice(c.device);
+  u64 *d_pv = (u64 *)dev_alloc(c, (size_t)g->n * 8);
+  if (!d_pv) return CC_ERR_OOM;
+  u64 cnt = 0;
+  bool ovf = false;
+  rc = run_plan(c, *g, *p, trial, &cnt, &ovf, d_pv);
+  if (rc == CC_OK) {
+    std::vector<u64> by_rank(g->n);
+    std::vector<int32_t> id_of(g->n);
+    if (cudaMemcpy(by_rank.data(), d_pv, g->n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(id_of.data(), g->id_of, g->n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      rc = CC_ERR_CUDA;
+    } else {
+      for (int64_t r = 0; r < g->n; r++) per_vertex[id_of[r]] = by_rank[r];
+      if (total) *total = ovf ? UINT64_MAX : cnt;
+      if (ovf) rc = CC_ERR_OVERFLOW;
+    }
+  }
+  dev_free(c, d_pv, (size_t)g->n * 8);
+  return rc;
+}
+
+int cc_work_units(cc_ctx *ctx, int32_t graph_id, int32_t query_id, double *units) {
+  DevGraph *g;
+  Plan *p;
+  int rc = lookup(ctx, graph_id, query_id, &g, &p);
+  if (rc != CC_OK) return rc;
+  if (!units) return CC_ERR_INVALID_ARG;
+  auto it = g->work_cache.find(query_id);
+  if (it != g->work_cache.end()) {
+    *units = it->second;
+    return CC_OK;
+  }
+  Ctx &c = ctx->c;
+  cudaSetDevice(c.device);
+  u64 cnt = 0;
+  bool ovf = false;
+  double w = 0.0;
+  // the structure (reach sets, wedges) does not depend on the colouring
+  rc = run_plan(c, *g, *p, 0, &cnt, &ovf, nullptr, &w);
+  if (rc != CC_OK) return rc;
+  g->work_cache[query_id] = w;
+  *units = w;
+  return CC_OK;
+}
+
+int cc_set_timing(cc_ctx *ctx, int enable) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  ctx->c.timing = enable != 0;
+  return CC_OK;
+}
+
+int cc_get_timing(cc_ctx *ctx, char *names, double *ms, int64_t *launches, int cap) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  timing_flush(ctx->c);
+  int i = 0;
+  for (auto &t : ctx->c.times) {
+    if (i >= cap) break;
+    if (names) {
+      strncpy(names + 48 * i, t.first.c_str(), 47);
+      names[48 * i + 47] = 0;
+    }
+    if (ms) ms[i] = t.second.first;
+    if (launches) launches[i] = t.second.second;
+    i++;
+  }
+  return (int)ctx->c.times.size();
+}
+
+int cc_reset_timing(cc_ctx *ctx) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  timing_flush(ctx->c);
+  ctx->c.times.clear();
+  return CC_OK;
+}
+
+}  // extern "C"

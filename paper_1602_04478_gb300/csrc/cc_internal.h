@@ -1,0 +1,102 @@
+// Internal declarations shared by the library's host translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/cc.h"
+
+namespace cc {
+
+constexpr int kMaxK = CC_MAX_K;
+constexpr int kMaxCycle = 8;  // longest root cycle the closure kernel handles
+
+// ------------------------------- query plan -------------------------------
+enum StageKind { ST_LEAF = 0, ST_TRI = 1, ST_CYCLE_ROOT = 2, ST_ROOT_NODE = 3 };
+
+// One block of the decomposition tree (Section 4.1) in contraction order.
+struct Stage {
+  int kind = 0;
+  int L = 0;                 // leaf: 2 (a, b); triangle: 3; root cycle: L
+  int nodes[kMaxK];          // leaf: a (boundary), b (leaf); cycle in cyclic order
+  int nb = 0;                // boundary nodes of the block (0, 1 or 2)
+  int bd[2] = {-1, -1};      // ordered: a 2-boundary table is keyed (img bd0 -> img bd1)
+  int node_child[kMaxK];     // per position: stage index of the annotating block, -1 none
+  int edge_child[kMaxK];     // per cycle edge nodes[i] -> nodes[i+1 mod L]
+  bool edge_fwd[kMaxK];      // child's first boundary node is nodes[i]
+  int s = 0;                 // |SQ(B)|: query nodes of the represented subquery
+  uint32_t sq_mask = 0;
+};
+
+struct Plan {
+  int k = 0;
+  std::vector<std::pair<int, int>> edges;
+  std::vector<Stage> stages;  // children before parents; the last stage is the root
+  int64_t aut = 0;
+  int longest_cycle = 0;
+  bool supported = false;
+};
+
+// Builds the default plan (searching decomposition orders) or applies an
+// explicit order.  Returns a CC_ status code.
+int plan_query(int k, const std::vector<std::pair<int, int>> &edges, Plan &out);
+int plan_explicit(int k, const std::vector<std::pair<int, int>> &edges,
+                  const std::vector<int> &block_seq, Plan &out);
+int64_t count_automorphisms(int k, const std::vector<std::pair<int, int>> &edges);
+
+// ------------------------------- data graph -------------------------------
+struct DevGraph {
+  int64_t n = 0, nnz = 0, max_deg = 0;
+  int64_t *row = nullptr;     // [n+1]  relabelled CSR (vertex = degree rank)
+  int32_t *col = nullptr;     // [nnz]  neighbour ranks, each row ascending
+  int64_t *rev = nullptr;     // [nnz]  position of the reverse directed edge
+  int32_t *lo_cnt = nullptr;  // [n]    neighbours with a smaller rank (a row prefix)
+  int32_t *id_of = nullptr;   // [n]    rank -> caller id
+  int32_t *rank_of = nullptr; // [n]    caller id -> rank
+  uint8_t *colors = nullptr;  // [T][n] explicit colours in rank order, or null
+  int colors_T = 0;
+  int colors_max = -1;        // largest explicit colour (must be below the query's k)
+  std::vector<int64_t> h_row;  // host copy of the relabelled row pointers
+  std::map<int, double> work_cache;  // query id -> structural work units
+};
+
+// -------------------------------- context --------------------------------
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cc_alloc_fn alloc = nullptr;
+  cc_free_fn free_fn = nullptr;
+  void *alloc_user = nullptr;
+  size_t budget = 0, in_use = 0;
+  uint64_t seed = 1;
+  std::map<int, DevGraph> graphs;
+  std::map<int, Plan> plans;
+  int next_graph = 1, next_query = 1;
+  // device scratch reused across calls
+  uint16_t *lut_rank = nullptr;    // [4096]
+  uint16_t *lut_unrank = nullptr;  // [13][924]
+  unsigned long long *d_status = nullptr;  // [4]: count lo, overflow flag, timeout flag, spare
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  uint64_t scratch_layout = 0;   // layout of the cycle kernel's scratch last used
+  bool scratch_dirty = true;     // contents unknown (fresh, or a launch failed)
+  unsigned epoch = 0;
+  // timing
+  bool timing = false;
+  std::map<std::string, std::pair<double, int64_t>> times;
+  std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+};
+
+void *dev_alloc(Ctx &c, size_t bytes);
+void dev_free(Ctx &c, void *p, size_t bytes);
+int ensure_scratch(Ctx &c, size_t bytes);
+
+// kernel-launch bracketing for the optional timing
+void timing_begin(Ctx &c, const char *name);
+void timing_end(Ctx &c);
+void timing_flush(Ctx &c);
+
+}  // namespace cc

@@ -1,0 +1,111 @@
+// Kernel argument blocks and launchers (host side of each .cu file).
+#pragma once
+#include "cc_device.cuh"
+#include "cc_internal.h"
+
+namespace cc {
+
+typedef unsigned long long u64;
+
+struct GraphView {
+  int64_t n = 0, nnz = 0;
+  const int64_t *row = nullptr;
+  const int32_t *col = nullptr;
+  const int64_t *rev = nullptr;
+  const int32_t *lo_cnt = nullptr;
+};
+
+// unary table [n][R] over signatures of size s (p == nullptr: no annotation)
+struct TabU {
+  const u64 *p = nullptr;
+  int s = 1;
+  int R = 1;
+};
+// edge-keyed table [nnz][R] over size-s signatures; use_rev: the row of a
+// traversal x -> y is rev[pos(x -> y)] instead of pos(x -> y)
+struct TabE {
+  const u64 *p = nullptr;
+  int s = 2;
+  int R = 1;
+  bool use_rev = false;
+};
+
+struct LeafArgs {
+  GraphView g;
+  const uint8_t *colors = nullptr;
+  int k = 0;
+  Lut lut;
+  TabU A, B;
+  TabE E;
+  int sY = 0, RY = 0;  // neighbour aggregate (edge x block at b)
+  u64 *out = nullptr;
+  int s_out = 0, R_out = 0;
+  u64 *status = nullptr;
+};
+
+struct TriArgs {
+  GraphView g;
+  const uint8_t *colors = nullptr;
+  int k = 0;
+  Lut lut;
+  TabU N[3];
+  TabE E[3];        // E[i]: triangle edge nodes[i] -> nodes[i+1]; use_rev for that direction
+  int nb = 0;       // output: 0 root count, 1 unary at bd0, 2 edge-keyed bd0 -> bd1
+  int bd[2] = {-1, -1};  // positions (0..2) of the boundary nodes
+  int s_out = 3, R_out = 1;
+  u64 *out = nullptr;
+  u64 *per_vertex = nullptr;  // root: count by highest vertex (rank order), nullable
+  u64 *status = nullptr;
+  int *work_counter = nullptr;
+  bool count_units = false;   // add the wedges scanned to status[ST_UNITS]
+};
+
+int launch_leaf(Ctx &c, const LeafArgs &a);
+int launch_root_sum(Ctx &c, const GraphView &g, const u64 *table, u64 *per_vertex, u64 *status);
+int launch_triangle(Ctx &c, const TriArgs &a);
+
+// root cycle (L >= 4) closure; see cycle.cu
+struct CycleArgs {
+  GraphView g;
+  const uint8_t *colors = nullptr;
+  int k = 0;
+  Lut lut;
+  int L = 0;
+  TabU N[kMaxCycle];
+  TabE Efw[kMaxCycle];   // edge i traversed nodes[i] -> nodes[i+1]
+  TabE Ebw[kMaxCycle];   // edge i traversed nodes[i+1] -> nodes[i]
+  int multiplier = 1;    // rotations folded into one highest-node choice
+  int n_h = 0;
+  int hs[kMaxCycle];
+  u64 *per_vertex = nullptr;  // count by highest vertex (rank order), nullable
+  u64 *status = nullptr;
+  bool count_units = false;   // add the structural edge-subset work to status[ST_UNITS]
+};
+int launch_cycle(Ctx &c, const CycleArgs &a);
+size_t cycle_scratch_bytes(const CycleArgs &a, int slots);
+
+int graph_load(Ctx &c, int64_t n, const int64_t *row_ptr, const int32_t *col, int64_t nnz, DevGraph &g);
+void graph_free(Ctx &c, DevGraph &g);
+int colors_fill(Ctx &c, const DevGraph &g, int k, int64_t trial, uint8_t *d_out);
+int colors_set(Ctx &c, DevGraph &g, const uint8_t *h_colors, int T);
+int luts_init(Ctx &c);
+
+inline GraphView view_of(const DevGraph &g) {
+  GraphView v;
+  v.n = g.n;
+  v.nnz = g.nnz;
+  v.row = g.row;
+  v.col = g.col;
+  v.rev = g.rev;
+  v.lo_cnt = g.lo_cnt;
+  return v;
+}
+
+inline int64_t binom(int a, int b) {
+  if (b < 0 || a < 0 || b > a) return 0;
+  int64_t r = 1;
+  for (int i = 1; i <= b; i++) r = r * (a - b + i) / i;
+  return r;
+}
+
+}  // namespace cc

@@ -1,0 +1,134 @@
+// K2: leaf-block join and K6: root-singleton reduction.
+//
+// Leaf block (a, b) with b a leaf (Section 5.2, "leaf blocks"): join the
+// tables of the blocks annotating node a, edge (a, b) and node b.  For a data
+// vertex x as the image of a:
+//   Y[x][S]   = sum over neighbours y of x of  E[(x,y)][S_E] * B[y][S_B]
+//               with S_E containing chi(x), chi(y), S_B containing chi(y),
+//               S_E and S_B sharing exactly chi(y), S = S_E u S_B;
+//   Out[x][S] = sum over S_A, S_Y with S_A and S_Y sharing exactly chi(x),
+//               S = S_A u S_Y, of A[x][S_A] * Y[x][S_Y].
+// A missing block is the identity (A: the single signature {chi(x)}; B:
+// {chi(y)}; E: the plain data edge with signature {chi(x), chi(y)}, count 1
+// when the two colours differ -- the B_G table of Section 5.2).
+// One warp per vertex; Y lives in shared memory.  The gather of B rows over
+// the CSR is the HBM traffic of this kernel.
+//
+// Root singleton (Section 5.2, last paragraph): sum the annotating block's
+// table over all vertices (its rows hold the single full signature).
+#include "cc_kernels.h"
+
+namespace cc {
+
+__global__ void __launch_bounds__(256) k_leaf_join(LeafArgs a) {
+  extern __shared__ u64 smem_y[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  u64 *Y = smem_y + (size_t)wib * a.RY;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned ovf = 0;
+  for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + wib; x < a.g.n; x += nwarps) {
+    const int cx = a.colors[x];
+    for (int i = lane; i < a.RY; i += 32) Y[i] = 0;
+    __syncwarp();
+    const int64_t rb = a.g.row[x], re = a.g.row[x + 1];
+    for (int64_t i = rb + lane; i < re; i += 32) {
+      const int32_t y = __ldg(a.g.col + i);
+      const int cy = a.colors[y];
+      if (cy == cx) continue;
+      const int nE = a.E.p ? a.E.R : 1;
+      const int64_t erow = a.E.p ? (a.E.use_rev ? __ldg(a.g.rev + i) : i) : 0;
+      for (int je = 0; je < nE; je++) {
+        uint32_t mE;
+        u64 vE;
+        if (a.E.p) {
+          vE = __ldg(a.E.p + erow * a.E.R + je);
+          if (!vE) continue;
+          mE = pmask(a.lut, a.E.s, je, cx, cy);
+        } else {
+          vE = 1;
+          mE = (1u << cx) | (1u << cy);
+        }
+        if (a.B.p) {
+          const u64 *brow = a.B.p + (int64_t)y * a.B.R;
+          for (int jb = 0; jb < a.B.R; jb++) {
+            u64 vB = __ldg(brow + jb);
+            if (!vB) continue;
+            uint32_t mB = umask(a.lut, a.B.s, jb, cy);
+            if ((mB & mE) != (1u << cy)) continue;
+            u64 v = mul_ck(vE, vB, ovf);
+            int slot = uslot(a.lut, mB | mE, cx);
+            unsigned long long old = atomicAdd(Y + slot, v);
+            ovf |= (old + v < old);
+          }
+        } else {
+          int slot = uslot(a.lut, mE, cx);
+          unsigned long long old = atomicAdd(Y + slot, vE);
+          ovf |= (old + vE < old);
+        }
+      }
+    }
+    __syncwarp();
+    u64 *orow = a.out + x * (int64_t)a.R_out;
+    if (!a.A.p) {
+      for (int o = lane; o < a.R_out; o += 32) orow[o] = Y[o];
+    } else {
+      const u64 *arow = a.A.p + x * (int64_t)a.A.R;
+      for (int o = lane; o < a.R_out; o += 32) {
+        uint32_t mO = umask(a.lut, a.s_out, o, cx);
+        u64 acc = 0;
+        for (int ja = 0; ja < a.A.R; ja++) {
+          u64 vA = __ldg(arow + ja);
+          if (!vA) continue;
+          uint32_t mA = umask(a.lut, a.A.s, ja, cx);
+          if (mA & ~mO) continue;
+          uint32_t mY = (mO & ~mA) | (1u << cx);
+          u64 vY = Y[uslot(a.lut, mY, cx)];
+          if (!vY) continue;
+          acc = add_ck(acc, mul_ck(vA, vY, ovf), ovf);
+        }
+        orow[o] = acc;
+      }
+    }
+    __syncwarp();
+  }
+  flag_overflow(a.status, ovf);
+}
+
+int launch_leaf(Ctx &c, const LeafArgs &a) {
+  size_t smem = (size_t)8 * a.RY * sizeof(u64);
+  if (smem > 200 * 1024) return CC_ERR_UNSUPPORTED;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_leaf_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int64_t blocks = (a.g.n + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  timing_begin(c, "leaf_join");
+  k_leaf_join<<<(unsigned)blocks, 256, smem, c.stream>>>(a);
+  timing_end(c);
+  return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+}
+
+__global__ void __launch_bounds__(256) k_root_sum(int64_t n, const u64 *table, u64 *per_vertex, u64 *status) {
+  unsigned ovf = 0;
+  u64 acc = 0;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    u64 v = table[x];
+    if (per_vertex) per_vertex[x] = v;
+    acc = add_ck(acc, v, ovf);
+  }
+  acc = warp_sum_ck(acc, ovf);
+  if ((threadIdx.x & 31) == 0) atomic_add_ck(status + ST_COUNT, acc, ovf);
+  flag_overflow(status, ovf);
+}
+
+int launch_root_sum(Ctx &c, const GraphView &g, const u64 *table, u64 *per_vertex, u64 *status) {
+  int64_t blocks = (g.n + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  timing_begin(c, "root_sum");
+  k_root_sum<<<(unsigned)blocks, 256, 0, c.stream>>>(g.n, table, per_vertex, status);
+  timing_end(c);
+  return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+}
+
+}  // namespace cc

@@ -1,0 +1,296 @@
+"""CUDA path against the CPU oracle: bit-exact uint64 colourful counts.
+
+Every count goes through the C-ABI (``paper_1602_04478_gb300`` binding) and is
+compared with ``oracle.dp_count`` (pinned to brute force and closed forms in
+test_oracle_pins.py) on the same seeded graph and the same colouring.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+QUERIES = dict(gg.QUERIES)
+QUERIES.update({
+    "path4": (4, [(0, 1), (1, 2), (2, 3)]),
+    "star4": (5, [(0, 1), (0, 2), (0, 3), (0, 4)]),
+    "tailed_triangle": (4, [(0, 1), (1, 2), (2, 0), (2, 3)]),
+    "bowtie": (5, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 2)]),
+    "house": (5, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (4, 1)]),
+    "chord_pendant0": (5, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 2), (0, 4)]),
+    "C6_2pendants_adj": (8, [(i, (i + 1) % 6) for i in range(6)] + [(0, 6), (1, 7)]),
+    "C6_2pendants_same": (8, [(i, (i + 1) % 6) for i in range(6)] + [(0, 6), (0, 7)]),
+    "C7": gg.cycle(7),
+    "C8": gg.cycle(8),
+    "triangle_strip": (5, [(0, 1), (1, 2), (2, 0), (1, 3), (2, 3), (2, 4), (3, 4)]),
+    "C5_pendant_path": (7, [(i, (i + 1) % 5) for i in range(5)] + [(0, 5), (5, 6)]),
+})
+
+
+@pytest.fixture(scope="module")
+def cc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1602_04478_gb300 as P
+    ctx = P.Context(0)
+    yield ctx
+    ctx.close()
+
+
+GRAPHS = {
+    "er60": lambda: gg.erdos_renyi(60, 300, 1),
+    "er2000": lambda: gg.erdos_renyi(2000, 10000, 1),
+    "cl3000": lambda: gg.chung_lu(3000, 8, 2.1, 3),
+    "rmat10": lambda: gg.rmat(10, 8, 0.57, 0.19, 0.19, 4),
+}
+_cache = {}
+
+
+def graph(name):
+    if name not in _cache:
+        _cache[name] = GRAPHS[name]()
+    return _cache[name]
+
+
+def gpu_count(cc, g, gid, k, edges, seed, trials):
+    import paper_1602_04478_gb300 as P
+    qid = cc.set_query(k, edges)
+    P.cc_set_coloring_seed(cc.h, seed)
+    col, est, aut = cc.count(gid, qid, 0, trials)
+    return col, est, aut, qid
+
+
+@pytest.mark.parametrize("gname", ["er60", "er2000", "cl3000", "rmat10"])
+@pytest.mark.parametrize("qname", sorted(QUERIES))
+def test_count_matches_oracle(cc, gname, qname):
+    g = graph(gname)
+    k, e = QUERIES[qname]
+    if gname != "er60" and k >= 7:
+        pytest.skip("k >= 7 runs on the 60-vertex graph (oracle time); larger graphs cover k <= 6")
+    gid = cc.load_graph(g)
+    try:
+        seed = 7
+        trials = 2
+        col, est, aut, qid = gpu_count(cc, g, gid, k, e, seed, trials)
+        assert aut == O.automorphisms(k, e)
+        for t in range(trials):
+            cols = O.colors(seed, t, g.n, k)
+            expect, ovf = O.dp_count(g, k, e, cols)
+            assert not ovf
+            assert int(col[t]) == expect, (qname, gname, t)
+            scale = k ** k / math.factorial(k) / aut
+            assert est[t] == pytest.approx(expect * scale, rel=1e-12)
+    finally:
+        cc.free_graph(gid)
+
+
+def test_explicit_colours_and_brute_force(cc):
+    import paper_1602_04478_gb300 as P
+    g = graph("er60")
+    gid = cc.load_graph(g)
+    try:
+        for qname in ["C5", "C6", "glasses", "chord_pendant", "C6_2pendants", "diamond"]:
+            k, e = QUERIES[qname]
+            rng = np.random.default_rng(3)
+            cols = rng.integers(0, k, size=(3, g.n)).astype(np.uint8)
+            P.cc_set_colors(cc.h, gid, cols)
+            qid = cc.set_query(k, e)
+            got, _, _ = cc.count(gid, qid, 0, 3)
+            for t in range(3):
+                assert int(got[t]) == O.brute_colorful(g, k, e, cols[t])
+            P.cc_clear_colors(cc.h, gid)
+    finally:
+        cc.free_graph(gid)
+
+
+@pytest.mark.parametrize("qname", ["C4", "C5", "C6", "C6_2pendants", "chord_pendant", "diamond", "glasses",
+                                   "C7", "C8"])
+def test_per_vertex_split_matches_oracle(cc, qname):
+    g = graph("er2000") if QUERIES[qname][0] < 7 else graph("er60")
+    k, e = QUERIES[qname]
+    import paper_1602_04478_gb300 as P
+    gid = cc.load_graph(g)
+    try:
+        qid = cc.set_query(k, e)
+        P.cc_set_coloring_seed(cc.h, 11)
+        pv, total = cc.count_per_vertex(gid, qid, 0)
+        cols = O.colors(11, 0, g.n, k)
+        expect, _, per = O.dp_count(g, k, e, cols, per_source=True)
+        assert total == expect == int(pv.sum())
+        info = P.cc_query_info(cc.h, qid)
+        # the split is by the root block: compare when the oracle's root is the same kind
+        blocks, root, _ = O.decompose(k, e)
+        if blocks[root]["kind"] == "root_cycle" and info["longest_cycle"] >= 3 and qname not in ("glasses",):
+            assert [int(x) for x in pv] == per
+    finally:
+        cc.free_graph(gid)
+
+
+def test_decomposition_invariance(cc):
+    import paper_1602_04478_gb300 as P
+    g = graph("er2000")
+    k, e = QUERIES["chord_pendant"]
+    orders = [
+        [0, 1, 4, 3, 0, 1, 2],   # leaf (1,4), then triangle (0,1,2); root triangle (0,2,3)
+        [3, 0, 2, 3, 0, 1, 4],   # triangle (0,2,3) first, then the leaf; root triangle (0,1,2)
+        [0, 1, 4, 3, 0, 2, 3],   # leaf, then triangle (0,2,3); root triangle (0,1,2)
+    ]
+    gid = cc.load_graph(g)
+    try:
+        P.cc_set_coloring_seed(cc.h, 5)
+        got = []
+        for seq in orders:
+            qid = cc.set_query(k, e)
+            P.cc_set_decomposition(cc.h, qid, seq)
+            got.append(int(cc.count(gid, qid, 0, 1)[0][0]))
+        expect = O.dp_count(g, k, e, O.colors(5, 0, g.n, k))[0]
+        assert got == [expect] * len(orders)
+    finally:
+        cc.free_graph(gid)
+
+
+def test_relabel_invariance(cc):
+    import paper_1602_04478_gb300 as P
+    g = graph("cl3000")
+    perm = np.random.default_rng(1).permutation(g.n)
+    h = gg.relabel(g, perm)
+    k, e = QUERIES["C5"]
+    cols = O.colors(2, 0, g.n, k)
+    colh = np.zeros_like(cols)
+    colh[perm] = cols
+    a, b = cc.load_graph(g), cc.load_graph(h)
+    try:
+        P.cc_set_colors(cc.h, a, cols)
+        P.cc_set_colors(cc.h, b, colh)
+        qid = cc.set_query(k, e)
+        assert int(cc.count(a, qid)[0][0]) == int(cc.count(b, qid)[0][0])
+    finally:
+        cc.free_graph(a)
+        cc.free_graph(b)
+
+
+# ------------------------------ edge cases ------------------------------
+def test_empty_and_tiny_graphs(cc):
+    import paper_1602_04478_gb300 as P
+    P.cc_set_coloring_seed(cc.h, 1)
+    for g in [gg.from_edges(5, []), gg.from_edges(3, [(0, 1)]), gg.from_edges(4, [(0, 1), (1, 2), (2, 0)])]:
+        gid = cc.load_graph(g)
+        try:
+            for qname in ["triangle", "C4", "glasses", "path4"]:
+                k, e = QUERIES[qname]
+                qid = cc.set_query(k, e)
+                got = cc.count(gid, qid, 0, 1)[0]
+                assert int(got[0]) == O.dp_count(g, k, e, O.colors(1, 0, g.n, k))[0]
+        finally:
+            cc.free_graph(gid)
+
+
+def test_complete_graph_closed_form(cc):
+    import paper_1602_04478_gb300 as P
+    g = gg.complete_graph(40)
+    gid = cc.load_graph(g)
+    try:
+        for L in (3, 4, 5, 6):
+            k, e = gg.cycle(L)
+            qid = cc.set_query(k, e)
+            P.cc_set_coloring_seed(cc.h, 9)
+            got = int(cc.count(gid, qid)[0][0])
+            nc = np.bincount(O.colors(9, 0, g.n, k), minlength=k).astype(object)
+            assert got == math.factorial(k) * int(np.prod(nc))
+    finally:
+        cc.free_graph(gid)
+
+
+@pytest.mark.parametrize("edges,code", [
+    ([(a, b) for a in range(4) for b in range(a + 1, 4)], "CC_ERR_NOT_TW2"),
+    ([(0, 1), (2, 3)], "CC_ERR_NOT_CONNECTED"),
+    ([(0, 1), (1, 0)], "CC_ERR_INVALID_ARG"),
+    ([(0, 0)], "CC_ERR_INVALID_ARG"),
+])
+def test_query_errors(cc, edges, code):
+    import paper_1602_04478_gb300 as P
+    k = 1 + max(max(x) for x in edges)
+    with pytest.raises(P.CCError) as ei:
+        cc.set_query(max(k, 2), edges)
+    assert P.ERRORS[ei.value.code] == code
+
+
+def test_k_range_error(cc):
+    import paper_1602_04478_gb300 as P
+    for k in (1, 13):
+        with pytest.raises(P.CCError) as ei:
+            cc.set_query(k, [(i, i + 1) for i in range(k - 1)] or [(0, 0)])
+        assert ei.value.code in (-4, -1)
+
+
+def test_unsupported_block_reported(cc):
+    # two 4-cycles sharing a node: one must be a non-root 4-cycle block
+    import paper_1602_04478_gb300 as P
+    e = [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (4, 5), (5, 6), (6, 0)]
+    with pytest.raises(P.CCError) as ei:
+        cc.set_query(7, e)
+    assert P.ERRORS[ei.value.code] == "CC_ERR_UNSUPPORTED"
+
+
+@pytest.mark.parametrize("bad", ["asym", "loop", "dup", "range"])
+def test_bad_graph_rejected(cc, bad):
+    import paper_1602_04478_gb300 as P
+    if bad == "asym":
+        rp, col = np.array([0, 1, 1, 1]), np.array([1])
+    elif bad == "loop":
+        rp, col = np.array([0, 2, 3, 4]), np.array([0, 1, 0, 0])
+    elif bad == "dup":
+        rp, col = np.array([0, 2, 4, 4]), np.array([1, 1, 0, 0])
+    else:
+        rp, col = np.array([0, 1, 2, 2]), np.array([7, 0])
+    with pytest.raises(P.CCError) as ei:
+        P.cc_load_csr(cc.h, 3, rp, col)
+    assert P.ERRORS[ei.value.code] == "CC_ERR_BAD_GRAPH"
+
+
+def test_overflow_reported_not_wrapped(cc):
+    import paper_1602_04478_gb300 as P
+    k = 12
+    e = [(0, i) for i in range(1, k)]
+    D = 3000
+    g = gg.from_edges(D + 1, [(0, i) for i in range(1, D + 1)])
+    gid = cc.load_graph(g)
+    try:
+        qid = cc.set_query(k, e)
+        P.cc_set_coloring_seed(cc.h, 1)
+        with pytest.raises(P.CCError) as ei:
+            cc.count(gid, qid, 0, 1)
+        assert P.ERRORS[ei.value.code] == "CC_ERR_OVERFLOW"
+        col, _, _ = cc.count(gid, qid, 0, 1, allow_overflow=True)
+        assert int(col[0]) == 2**64 - 1
+        assert O.dp_count(g, k, e, O.colors(1, 0, g.n, k))[1]
+    finally:
+        cc.free_graph(gid)
+
+
+def test_memory_budget_oom(cc):
+    # admission by table memory: the edge-keyed table of chord_pendant
+    # (nnz x 3 x 8 bytes) does not fit the budget, so the count is refused
+    # before any launch and the context stays usable
+    import paper_1602_04478_gb300 as P
+    ctx = P.Context(0)
+    try:
+        g = gg.chung_lu(200000, 16, 2.1, 2)
+        gid = ctx.load_graph(g)
+        qid = ctx.set_query(*QUERIES["chord_pendant"])
+        P.cc_set_memory_budget(ctx.h, 64 << 20)
+        with pytest.raises(P.CCError) as ei:
+            ctx.count(gid, qid)
+        assert P.ERRORS[ei.value.code] == "CC_ERR_OOM"
+        P.cc_set_memory_budget(ctx.h, 0)
+        k, e = QUERIES["chord_pendant"]
+        got = int(ctx.count(gid, qid)[0][0])
+        P.cc_set_coloring_seed(ctx.h, 1)
+        assert got == int(ctx.count(gid, qid)[0][0])
+    finally:
+        ctx.close()

@@ -1,0 +1,111 @@
+"""Host-side query planning of the CUDA library, checked on the CPU.
+
+cc_plan_inspect runs the library's own decomposition (Section 4.1, Cases 1-3)
+and aut(Q) without a device.  Checks: aut(Q) equals the oracle's enumeration,
+every plan is a well-formed decomposition tree, an explicit order reproduces
+the paper's worked Satellite tree, and treewidth-3 queries are rejected.
+"""
+import os
+
+import pytest
+
+import graphgen as gg
+import oracle as O
+import paper_1602_04478_gb300 as P
+
+from test_oracle_pins import EXTRA, _read_satellite, _same_cycle
+
+QUERIES = dict(gg.QUERIES)
+QUERIES.update(EXTRA)
+
+
+@pytest.mark.parametrize("name", sorted(QUERIES))
+def test_aut_and_plan_shape(name):
+    k, e = QUERIES[name]
+    try:
+        blocks, aut = P.cc_plan_inspect(k, e)
+    except P.CCError as ex:
+        assert P.ERRORS[ex.code] == "CC_ERR_UNSUPPORTED"
+        return
+    assert aut == O.automorphisms(k, e)
+    covered = set()
+    edges = {tuple(sorted(x)) for x in e}
+    seen_children = set()
+    for i, b in enumerate(blocks):
+        for c in b["children"]:
+            assert c < i and c not in seen_children  # each block has one parent, built before it
+            seen_children.add(c)
+        if b["kind"] in ("triangle", "root_cycle", "cycle"):
+            L = len(b["nodes"])
+            assert (L == 3) == (b["kind"] == "triangle")
+        covered.update(b["nodes"])
+    assert covered == set(range(k))
+    assert blocks[-1]["kind"] in ("root_cycle", "root_node", "triangle")
+    assert len(seen_children) == len(blocks) - 1  # a tree: every block but the root is a child
+    # every original edge lies in some block as a leaf edge or a cycle edge
+    block_edges = set()
+    for b in blocks:
+        nodes = b["nodes"]
+        if b["kind"] == "leaf":
+            block_edges.add(tuple(sorted(nodes)))
+        elif b["kind"] != "root_node":
+            for i in range(len(nodes)):
+                block_edges.add(tuple(sorted((nodes[i], nodes[(i + 1) % len(nodes)]))))
+    assert edges <= block_edges
+
+
+def test_satellite_explicit_order_reproduces_paper_tree():
+    edges, expect = _read_satellite()
+    # B1 = 5-cycle a..e, B2 = leaf (f,h), B3 = 4-cycle (a,f,g,c), B4 = triangle (i,j,k)
+    seq = [5, 0, 1, 2, 3, 4, 0, 5, 7, 4, 0, 5, 6, 2, 3, 8, 9, 10]
+    with pytest.raises(P.CCError) as ei:
+        P.cc_plan_inspect(11, edges, seq)
+    # non-root cycles longer than a triangle have no kernel yet
+    assert P.ERRORS[ei.value.code] == "CC_ERR_UNSUPPORTED"
+    blocks, _ = _inspect_anyway(11, edges, seq)
+    names = {}
+    for i, (blk, (name, kind, nodes, bd, kids)) in enumerate(zip(blocks, expect)):
+        names[name] = i
+        want_kind = {"cycle": ("cycle", "triangle"), "leaf": ("leaf",), "root_cycle": ("triangle", "root_cycle")}
+        assert blk["kind"] in want_kind[kind]
+        if kind == "leaf":
+            assert blk["nodes"] == nodes
+        else:
+            assert _same_cycle(blk["nodes"], nodes)
+        assert sorted(blk["boundary"]) == sorted(bd)
+        assert sorted(blk["children"]) == sorted(names[c] for c in kids)
+    assert len(blocks) == len(expect)
+
+
+def _inspect_anyway(k, edges, seq):
+    return P.cc_plan_inspect(k, edges, seq, allow_unsupported=True)
+
+
+@pytest.mark.parametrize("edges", [
+    [(a, b) for a in range(4) for b in range(a + 1, 4)],
+    [(a, b) for a in range(5) for b in range(a + 1, 5) if (a, b) != (0, 1)],
+])
+def test_treewidth3_rejected(edges):
+    k = 1 + max(max(x) for x in edges)
+    with pytest.raises(P.CCError) as ei:
+        P.cc_plan_inspect(k, edges)
+    assert P.ERRORS[ei.value.code] == "CC_ERR_NOT_TW2"
+
+
+def test_explicit_orders_of_chord_pendant():
+    k, e = QUERIES["chord_pendant"]
+    b1, _ = P.cc_plan_inspect(k, e, [0, 1, 4, 3, 0, 1, 2])
+    assert [x["kind"] for x in b1] == ["leaf", "triangle", "triangle"]
+    assert sorted(b1[1]["boundary"]) == [0, 2] and b1[1]["children"] == [0]
+    b2, _ = P.cc_plan_inspect(k, e, [3, 0, 2, 3, 0, 1, 4])
+    assert [x["kind"] for x in b2] == ["triangle", "leaf", "triangle"]
+    assert sorted(b2[-1]["children"]) == [0, 1]
+    with pytest.raises(P.CCError):
+        P.cc_plan_inspect(k, e, [3, 0, 1, 3])  # (0,1,3) is not a cycle of the query
+
+
+def test_default_plans_of_workload_queries_are_supported():
+    for name in ["C4", "C5", "C6", "diamond", "chord_pendant", "glasses", "C6_2pendants"]:
+        k, e = QUERIES[name]
+        blocks, _ = P.cc_plan_inspect(k, e)
+        assert all(b["kind"] != "cycle" for b in blocks)
