@@ -75,6 +75,12 @@ int cc_set_allocator(cc_ctx *ctx, cc_alloc_fn alloc, cc_free_fn free_fn, void *u
  * launch. */
 int cc_set_memory_budget(cc_ctx *ctx, size_t bytes);
 
+/* Heavy/light split of the root-cycle closure: sources (highest cycle
+ * vertices) of degree >= `degree` are processed in groups by the whole GPU,
+ * the others one per CTA.  -1 restores the library's choice.  The split
+ * changes only the speed, never the counts. */
+int cc_set_heavy_degree(cc_ctx *ctx, int degree);
+
 /* Copy a data graph to the device.  row_ptr[n+1] (int64) and col[nnz]
  * (int32, caller's vertex ids) describe a symmetric simple graph: each
  * undirected edge appears in both rows, no self-loops, no duplicates.

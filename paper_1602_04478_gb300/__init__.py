@@ -29,7 +29,8 @@ ERRORS = {
     -9: "CC_ERR_UNSUPPORTED", -10: "CC_ERR_NOT_CONNECTED",
 }
 EXPORTED = [
-    "cc_create", "cc_destroy", "cc_set_allocator", "cc_set_memory_budget", "cc_load_csr", "cc_free_graph",
+    "cc_create", "cc_destroy", "cc_set_allocator", "cc_set_memory_budget", "cc_set_heavy_degree",
+    "cc_load_csr", "cc_free_graph",
     "cc_graph_info", "cc_set_query", "cc_set_decomposition", "cc_plan_inspect", "cc_query_info", "cc_set_coloring_seed",
     "cc_set_colors", "cc_clear_colors", "cc_count", "cc_count_per_vertex", "cc_work_units", "cc_set_timing",
     "cc_get_timing", "cc_reset_timing", "cc_strerror",
@@ -68,6 +69,7 @@ def lib():
             "cc_destroy": ([P], None),
             "cc_set_allocator": ([P, ALLOC_FN, FREE_FN, P], ctypes.c_int),
             "cc_set_memory_budget": ([P, ctypes.c_size_t], ctypes.c_int),
+            "cc_set_heavy_degree": ([P, ctypes.c_int], ctypes.c_int),
             "cc_load_csr": ([P, I64, I64P, I32P, I64, I32P], ctypes.c_int),
             "cc_free_graph": ([P, I32], ctypes.c_int),
             "cc_graph_info": ([P, I32, I64P, I64P, I64P], ctypes.c_int),
@@ -122,6 +124,10 @@ def cc_set_allocator(h, alloc, free, user=None) -> None:
 
 def cc_set_memory_budget(h, nbytes: int) -> None:
     _check(lib().cc_set_memory_budget(h, nbytes), "cc_set_memory_budget")
+
+
+def cc_set_heavy_degree(h, degree: int) -> None:
+    _check(lib().cc_set_heavy_degree(h, degree), "cc_set_heavy_degree")
 
 
 def cc_load_csr(h, n: int, row_ptr: np.ndarray, col: np.ndarray) -> int:

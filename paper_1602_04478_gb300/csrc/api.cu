@@ -168,6 +168,7 @@ int run_plan(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, u64 *count, bool
   }
   Lut lut{c.lut_rank, c.lut_unrank};
   GraphView gv = view_of(g);
+  c.cur_graph_row = g.h_row.data();
   for (size_t i = 0; i < p.stages.size() && rc == CC_OK; i++) {
     const Stage &st = p.stages[i];
     bool is_root = i + 1 == p.stages.size();
@@ -341,6 +342,7 @@ void cc_destroy(cc_ctx *ctx) {
   cudaStreamSynchronize(c.stream);
   for (auto &g : c.graphs) graph_free(c, g.second);
   dev_free(c, c.scratch, c.scratch_bytes);
+  dev_free(c, c.hv_scratch, c.hv_scratch_bytes);
   dev_free(c, c.lut_rank, 4096 * 2);
   dev_free(c, c.lut_unrank, 13 * kUnrankStride * 2);
   dev_free(c, c.d_status, 64);
@@ -362,6 +364,12 @@ int cc_set_allocator(cc_ctx *ctx, cc_alloc_fn alloc, cc_free_fn free_fn, void *u
   c.d_status = (u64 *)dev_alloc(c, 64);
   if (!c.d_status) return CC_ERR_OOM;
   return luts_init(c);
+}
+
+int cc_set_heavy_degree(cc_ctx *ctx, int degree) {
+  if (!ctx || degree < -1) return CC_ERR_INVALID_ARG;
+  ctx->c.heavy_degree = degree;
+  return CC_OK;
 }
 
 int cc_set_memory_budget(cc_ctx *ctx, size_t bytes) {

@@ -84,6 +84,11 @@ struct Ctx {
   uint64_t scratch_layout = 0;   // layout of the cycle kernel's scratch last used
   bool scratch_dirty = true;     // contents unknown (fresh, or a launch failed)
   unsigned epoch = 0;
+  void *hv_scratch = nullptr;    // heavy-source cycle scratch
+  size_t hv_scratch_bytes = 0;
+  uint64_t hv_layout = 0;
+  const int64_t *cur_graph_row = nullptr;  // host row pointers of the graph being counted
+  int heavy_degree = -1;         // sources of at least this degree take the heavy path (-1: default)
   // timing
   bool timing = false;
   std::map<std::string, std::pair<double, int64_t>> times;

@@ -80,7 +80,10 @@ struct CycleArgs {
   u64 *per_vertex = nullptr;  // count by highest vertex (rank order), nullable
   u64 *status = nullptr;
   bool count_units = false;   // add the structural edge-subset work to status[ST_UNITS]
+  int32_t light_end = 0;      // the per-CTA kernel takes sources of rank < light_end
 };
+int run_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank, int B);
+int heavy_group_size(const CycleArgs &a);
 int launch_cycle(Ctx &c, const CycleArgs &a);
 size_t cycle_scratch_bytes(const CycleArgs &a, int slots);
 

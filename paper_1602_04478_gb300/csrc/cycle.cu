@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
   const int rp = L / 2, rm = L - L / 2;
   while (true) {
     if (tid == 0) {
-      s_u = (int)(a.g.n - 1 - atomicAdd(work_counter, 1));
+      s_u = (int)(a.light_end - 1 - atomicAdd(work_counter, 1));
       s_total = 0;
       s_ovf = 0;
     }
@@ -546,8 +546,25 @@ static CycleScratch plan_scratch(const CycleArgs &a, int slots) {
 
 size_t cycle_scratch_bytes(const CycleArgs &a, int slots) { return plan_scratch(a, slots).slot_bytes * (size_t)slots; }
 
-int launch_cycle(Ctx &c, const CycleArgs &a) {
-  if (a.L < 4 || a.L > kMaxCycle) return CC_ERR_UNSUPPORTED;
+int launch_cycle(Ctx &c, const CycleArgs &a_in) {
+  if (a_in.L < 4 || a_in.L > kMaxCycle) return CC_ERR_UNSUPPORTED;
+  CycleArgs a = a_in;
+  // sources of degree >= heavy_degree go to the grouped heavy path
+  const int64_t n = a.g.n;
+  int hd = c.heavy_degree >= 0 ? c.heavy_degree : 512;
+  if (a.count_units) hd = 1 << 30;  // structural counting runs on the per-CTA path only
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) / 2;
+    if (c.cur_graph_row[mid + 1] - c.cur_graph_row[mid] >= hd) hi = mid;
+    else lo = mid + 1;
+  }
+  a.light_end = (int32_t)lo;
+  if (a.light_end < n) {
+    int rc = run_heavy(c, a, a.light_end, heavy_group_size(a));
+    if (rc != CC_OK) return rc;
+  }
+  if (a.light_end == 0) return CC_OK;
   CycleScratch one = plan_scratch(a, 1);
   // slots: as many CTAs as memory allows, up to 4 per SM
   size_t budget = c.budget ? (c.budget > c.in_use ? c.budget - c.in_use : 0) : ((size_t)24 << 30);

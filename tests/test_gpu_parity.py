@@ -89,6 +89,29 @@ def test_count_matches_oracle(cc, gname, qname):
         cc.free_graph(gid)
 
 
+@pytest.mark.parametrize("heavy", [0, 3, 12, 1 << 30])
+@pytest.mark.parametrize("qname", ["C4", "C5", "C6", "C6_2pendants", "C6_2pendants_adj", "C7", "C8",
+                                   "C5_pendant_path"])
+def test_heavy_light_split(cc, heavy, qname):
+    # every source through the grouped heavy path (0), mixed splits, or the
+    # per-CTA path only: identical counts, equal to the oracle's
+    import paper_1602_04478_gb300 as P
+    k, e = QUERIES[qname]
+    g = graph("cl3000") if k <= 6 else graph("er60")
+    gid = cc.load_graph(g)
+    try:
+        P.cc_set_heavy_degree(cc.h, heavy)
+        P.cc_set_coloring_seed(cc.h, 4)
+        qid = cc.set_query(k, e)
+        pv, total = cc.count_per_vertex(gid, qid, 0)
+        expect, _, per = O.dp_count(g, k, e, O.colors(4, 0, g.n, k), per_source=True)
+        assert total == expect
+        assert [int(x) for x in pv] == per
+    finally:
+        P.cc_set_heavy_degree(cc.h, -1)
+        cc.free_graph(gid)
+
+
 def test_explicit_colours_and_brute_force(cc):
     import paper_1602_04478_gb300 as P
     g = graph("er60")
