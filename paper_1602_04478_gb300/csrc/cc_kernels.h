@@ -83,6 +83,9 @@ struct CycleArgs {
   int32_t light_end = 0;      // the per-CTA kernel takes sources of rank < light_end
 };
 int run_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank, int B);
+bool plain_cycle_eligible(const CycleArgs &a);
+int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank);
+int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank);
 int heavy_group_size(const CycleArgs &a);
 int launch_cycle(Ctx &c, const CycleArgs &a);
 size_t cycle_scratch_bytes(const CycleArgs &a, int slots);

@@ -551,7 +551,7 @@ int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   CycleArgs a = a_in;
   // sources of degree >= heavy_degree go to the grouped heavy path
   const int64_t n = a.g.n;
-  int hd = c.heavy_degree >= 0 ? c.heavy_degree : 512;
+  int hd = c.heavy_degree >= 0 ? c.heavy_degree : 256;
   if (a.count_units) hd = 1 << 30;  // structural counting runs on the per-CTA path only
   int64_t lo = 0, hi = n;
   while (lo < hi) {
@@ -560,11 +560,17 @@ int launch_cycle(Ctx &c, const CycleArgs &a_in) {
     else lo = mid + 1;
   }
   a.light_end = (int32_t)lo;
+  // plain C4..C6: 16-bit level-2 rows on the heavy path need max degree < 2^16
+  const bool plain = plain_cycle_eligible(a) && !a.count_units && (c.cur_graph_row[n] - c.cur_graph_row[n - 1]) < 65536;
   if (a.light_end < n) {
-    int rc = run_heavy(c, a, a.light_end, heavy_group_size(a));
+    int rc = plain ? run_plain_heavy(c, a, a.light_end) : run_heavy(c, a, a.light_end, heavy_group_size(a));
     if (rc != CC_OK) return rc;
   }
   if (a.light_end == 0) return CC_OK;
+  // plain C4..C6 below the threshold: per-CTA push with u32 level-3 rows,
+  // exact while max_degree * threshold < 2^32
+  if (plain && (double)(c.cur_graph_row[n] - c.cur_graph_row[n - 1]) * (double)hd < 4294967295.0)
+    return run_plain_light(c, a, a.light_end);
   CycleScratch one = plan_scratch(a, 1);
   // slots: as many CTAs as memory allows, up to 4 per SM
   size_t budget = c.budget ? (c.budget > c.in_use ? c.budget - c.in_use : 0) : ((size_t)24 << 30);

@@ -112,7 +112,59 @@ __device__ void tri_emit_general(const TriArgs &a, const int32_t vx[3], const in
   }
 }
 
-__global__ void __launch_bounds__(256) k_triangle(TriArgs a, bool plain) {
+// One annotation only (a node table at position ai, or an edge table on edge
+// ai -> ai+1): each of its row's signatures extends the triangle's colours
+// directly, without partial lists.
+__device__ __forceinline__ void tri_emit_one(const TriArgs &a, const int32_t vx[3], const int c[3],
+                                             const TriEdges &te, u64 &root_acc, unsigned &ovf, int ai, bool edge) {
+  const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const uint32_t K = (1u << a.k) - 1u;
+  for (int pi = 0; pi < 6; pi++) {
+    const int *p = perms[pi];
+    const uint32_t base = (1u << c[p[0]]) | (1u << c[p[1]]) | (1u << c[p[2]]);
+    const int li = p[ai], lj = p[(ai + 1) % 3];
+    const u64 *row;
+    int R, s;
+    uint32_t shared;
+    if (edge) {
+      const TabE &E = a.E[ai];
+      int64_t e = E.use_rev ? te.pos[lj][li] : te.pos[li][lj];
+      row = E.p + e * E.R;
+      R = E.R;
+      s = E.s;
+      shared = (1u << c[li]) | (1u << c[lj]);
+    } else {
+      const TabU &N = a.N[ai];
+      row = N.p + (int64_t)vx[li] * N.R;
+      R = N.R;
+      s = N.s;
+      shared = 1u << c[li];
+    }
+    if (a.nb == 0) {
+      // the root's signature is the full colour set: one compatible slot
+      uint32_t m = (K & ~base) | shared;
+      int slot = edge ? pslot(a.lut, m, c[li], c[lj]) : uslot(a.lut, m, c[li]);
+      root_acc = add_ck(root_acc, __ldg(row + slot), ovf);
+      continue;
+    }
+    for (int j = 0; j < R; j++) {
+      u64 t = __ldg(row + j);
+      if (!t) continue;
+      uint32_t mt = edge ? pmask(a.lut, s, j, c[li], c[lj]) : umask(a.lut, s, j, c[li]);
+      if ((mt & base) != shared) continue;
+      uint32_t m = mt | base;
+      if (a.nb == 1) {
+        int lb = p[a.bd[0]];
+        atomic_add_ck(a.out + (int64_t)vx[lb] * a.R_out + uslot(a.lut, m, c[lb]), t, ovf);
+      } else {
+        int l0 = p[a.bd[0]], l1 = p[a.bd[1]];
+        atomic_add_ck(a.out + te.pos[l0][l1] * a.R_out + pslot(a.lut, m, c[l0], c[l1]), t, ovf);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_triangle(TriArgs a, bool plain, int one_pos, bool one_edge) {
   const int lane = threadIdx.x & 31;
   unsigned ovf = 0;
   while (true) {
@@ -151,6 +203,7 @@ __global__ void __launch_bounds__(256) k_triangle(TriArgs a, bool plain) {
         te.pos[2][1] = __ldg(a.g.rev + te.pos[1][2]);
         te.pos[0][0] = te.pos[1][1] = te.pos[2][2] = -1;
         if (plain) tri_emit_plain(a, vx, c, te, root_acc, ovf);
+        else if (one_pos >= 0) tri_emit_one(a, vx, c, te, root_acc, ovf, one_pos, one_edge);
         else tri_emit_general(a, vx, c, te, root_acc, ovf);
       }
     }
@@ -169,10 +222,17 @@ __global__ void __launch_bounds__(256) k_triangle(TriArgs a, bool plain) {
 
 int launch_triangle(Ctx &c, const TriArgs &a) {
   bool plain = true;
-  for (int i = 0; i < 3; i++) plain = plain && !a.N[i].p && !a.E[i].p;
+  int n_ann = 0, one_pos = -1;
+  bool one_edge = false;
+  for (int i = 0; i < 3; i++) {
+    plain = plain && !a.N[i].p && !a.E[i].p;
+    if (a.N[i].p) n_ann++, one_pos = i, one_edge = false;
+    if (a.E[i].p) n_ann++, one_pos = i, one_edge = true;
+  }
+  if (n_ann != 1) one_pos = -1;
   if (cudaMemsetAsync(a.work_counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
-  timing_begin(c, plain ? "triangle_plain" : "triangle_join");
-  k_triangle<<<152 * 8, 256, 0, c.stream>>>(a, plain);
+  timing_begin(c, plain ? "triangle_plain" : (one_pos >= 0 ? "triangle_join1" : "triangle_join"));
+  k_triangle<<<152 * 8, 256, 0, c.stream>>>(a, plain, one_pos, one_edge);
   timing_end(c);
   return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }
