@@ -168,6 +168,31 @@ int cc_set_timing(cc_ctx *ctx, int enable);
 int cc_get_timing(cc_ctx *ctx, char *names, double *ms, int64_t *launches, int cap);
 int cc_reset_timing(cc_ctx *ctx);
 
+/* Count without any device allocation by the library (the paper has no
+ * counterpart; it is for callers that cannot let a library allocate GPU
+ * memory, e.g. code that owns a fixed device arena or runs where cudaMalloc
+ * is not allowed).  Counts colourful matches of the plain cycle C_L,
+ * L in {4, 5, 6} (k = L colours), in a graph given by DEVICE pointers:
+ * d_row_ptr[n+1] (int64) and d_col[nnz] (int32) a symmetric simple CSR whose
+ * rows are sorted ascending, d_colors[n] colours in 0..L-1.  *count (host)
+ * receives the count, equal to cc_count's for the same graph, colours and
+ * query.  Working memory is one static device array of 64 MiB inside the
+ * library, held by every GPU that loads it until the process exits; the
+ * graph must fit in it: n * 112 bytes (L = 5, 6) or n * 44 bytes (L = 4)
+ * plus n * 4 bytes and 256 bytes at most 64 MiB, else CC_ERR_INVALID_ARG.
+ * Maximum degree must stay below 65536 (CC_ERR_INVALID_ARG otherwise);
+ * unsorted rows, out-of-range ids, self-loops or colours >= L give
+ * CC_ERR_BAD_GRAPH.  Work is issued on cuda_stream (a cudaStream_t, NULL for
+ * the legacy stream) and the call returns when the count is on the host.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture on
+ * that device.  All calls share the one array (each call clears what it
+ * uses first), so calls that overlap on the GPU -- concurrent streams or
+ * threads -- race and must be serialised by the caller.  The calling
+ * thread's current device is restored on return. */
+int cc_count_cycle_noalloc(int device, void *cuda_stream, int L, int64_t n, const int64_t *d_row_ptr,
+                           const int32_t *d_col, const uint8_t *d_colors, uint64_t *count);
+
 const char *cc_strerror(int code);
 
 #ifdef __cplusplus

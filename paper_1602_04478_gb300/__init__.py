@@ -33,7 +33,7 @@ EXPORTED = [
     "cc_load_csr", "cc_free_graph",
     "cc_graph_info", "cc_set_query", "cc_set_decomposition", "cc_plan_inspect", "cc_query_info", "cc_set_coloring_seed",
     "cc_set_colors", "cc_clear_colors", "cc_count", "cc_count_per_vertex", "cc_work_units", "cc_set_timing",
-    "cc_get_timing", "cc_reset_timing", "cc_strerror",
+    "cc_get_timing", "cc_reset_timing", "cc_count_cycle_noalloc", "cc_strerror",
 ]
 
 _lib = None
@@ -88,6 +88,7 @@ def lib():
             "cc_set_timing": ([P, ctypes.c_int], ctypes.c_int),
             "cc_get_timing": ([P, ctypes.c_char_p, DP, I64P, ctypes.c_int], ctypes.c_int),
             "cc_reset_timing": ([P], ctypes.c_int),
+            "cc_count_cycle_noalloc": ([ctypes.c_int, P, ctypes.c_int, I64, P, P, P, U64P], ctypes.c_int),
             "cc_strerror": ([ctypes.c_int], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -275,6 +276,21 @@ def cc_get_timing(h, cap: int = 64):
 
 def cc_reset_timing(h) -> None:
     _check(lib().cc_reset_timing(h), "cc_reset_timing")
+
+
+def cc_count_cycle_noalloc(device: int, stream: int | None, L: int, n: int, d_row_ptr: int, d_col: int,
+                           d_colors: int) -> int:
+    """Plain-cycle colourful count with no device allocation by the library.
+
+    For callers that cannot let a library allocate GPU memory: inputs are
+    device addresses (sorted CSR rows, colours) the caller owns; the
+    library's working memory is a fixed 64 MiB static device array.  Calls
+    that overlap on the GPU share that array and race."""
+    out = ctypes.c_uint64(0)
+    _check(lib().cc_count_cycle_noalloc(device, ctypes.c_void_p(stream or 0), L, n, ctypes.c_void_p(d_row_ptr),
+                                        ctypes.c_void_p(d_col), ctypes.c_void_p(d_colors), ctypes.byref(out)),
+           "cc_count_cycle_noalloc")
+    return out.value
 
 
 def cc_strerror(code: int) -> str:

@@ -86,6 +86,15 @@ int run_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank, int B);
 bool plain_cycle_eligible(const CycleArgs &a);
 int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank);
 int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank);
+
+// scratch slots of the per-CTA plain-cycle push kernel (one slot per CTA)
+struct PlScratch {
+  char *base;
+  size_t slot_bytes;
+  size_t o_w2, o_w3, o_mark, o_l2, o_l3;
+};
+int launch_pc_light_raw(cudaStream_t stream, int L, const GraphView &g, const uint8_t *colors, const PlScratch &S,
+                        int slots, int32_t end_rank, int *work, u64 *status, int k);
 int heavy_group_size(const CycleArgs &a);
 int launch_cycle(Ctx &c, const CycleArgs &a);
 size_t cycle_scratch_bytes(const CycleArgs &a, int slots);

@@ -273,11 +273,7 @@ __global__ void k_pc_finish(PcScratch S, PcGroup G, int multiplier, u64 *per_ver
 // deg(x) * deg(u), which the host checks stays below 2^32.
 constexpr int kPlThreads = 256;
 
-struct PlScratch {
-  char *base;
-  size_t slot_bytes;
-  size_t o_w2, o_w3, o_mark, o_l2, o_l3;
-};
+
 
 __device__ __forceinline__ int pair_idx(int a, int b) {
   int hi = a > b ? a : b, lo = a > b ? b : a;
@@ -421,6 +417,22 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
     }
     __syncthreads();
   }
+}
+
+// Launch the per-CTA push kernel on caller-provided scratch (no allocation
+// here): `slots` CTAs, scratch slots laid out from S.base, *work zeroed by
+// the caller, sources 0 .. end_rank-1 (the highest first).
+int launch_pc_light_raw(cudaStream_t stream, int L, const GraphView &g, const uint8_t *colors, const PlScratch &S,
+                        int slots, int32_t end_rank, int *work, u64 *status, int k) {
+  if (L == 4)
+    k_pc_light<4><<<slots, kPlThreads, 0, stream>>>(g, colors, S, end_rank, work, L, nullptr, status, k);
+  else if (L == 5)
+    k_pc_light<5><<<slots, kPlThreads, 0, stream>>>(g, colors, S, end_rank, work, L, nullptr, status, k);
+  else if (L == 6)
+    k_pc_light<6><<<slots, kPlThreads, 0, stream>>>(g, colors, S, end_rank, work, L, nullptr, status, k);
+  else
+    return CC_ERR_INVALID_ARG;
+  return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }
 
 int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank) {
