@@ -147,6 +147,32 @@ int cc_clear_colors(cc_ctx *ctx, int32_t graph_id);
 int cc_count(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int first_trial, int T,
              uint64_t *colorful, double *estimate, double *aut);
 
+/* Batched form.  A request asks for trials first_trial .. first_trial +
+ * trials - 1 of one query on one graph.  All (request, trial) passes run on
+ * the device back to back with no host round trip between them; the first
+ * call for a given batch also records them as a CUDA graph, and later calls
+ * with the same requests (same seed and threshold) replay that graph as one
+ * launch.  colorful receives the counts of all trials, request after request
+ * (sum of `trials` entries, UINT64_MAX for an overflowing trial); status
+ * (nullable, n_reqs entries) receives CC_OK or CC_ERR_OVERFLOW per request.
+ * Counts are identical to cc_count's.  Returns CC_OK unless a request is
+ * invalid or a CUDA / memory error occurs. */
+typedef struct cc_request {
+  int32_t graph_id;
+  int32_t query_id;
+  int32_t first_trial;
+  int32_t trials;
+} cc_request;
+int cc_count_batch(cc_ctx *ctx, const cc_request *reqs, int n_reqs, uint64_t *colorful, int *status);
+/* Whether cc_count_batch records and replays CUDA graphs (default 1). */
+int cc_set_graph_capture(cc_ctx *ctx, int enable);
+/* Time the root-cycle closure of query_id on graph_id for heavy-source
+ * degree thresholds 64, 128, ..., 4096 (up to twice the maximum degree) on
+ * one colouring and keep the fastest for this (graph, query); later counts
+ * use it unless cc_set_heavy_degree forces a value.  *heavy_degree
+ * (nullable) receives the choice. */
+int cc_autotune(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int *heavy_degree);
+
 /* One trial, and the count split by vertex: for a root cycle block the
  * colourful matches whose highest root-cycle vertex (degree order) is v;
  * for a root that is a single node, the matches mapping that node to v.

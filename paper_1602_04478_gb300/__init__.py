@@ -33,8 +33,14 @@ EXPORTED = [
     "cc_load_csr", "cc_free_graph",
     "cc_graph_info", "cc_set_query", "cc_set_decomposition", "cc_plan_inspect", "cc_query_info", "cc_set_coloring_seed",
     "cc_set_colors", "cc_clear_colors", "cc_count", "cc_count_per_vertex", "cc_work_units", "cc_set_timing",
-    "cc_get_timing", "cc_reset_timing", "cc_count_cycle_noalloc", "cc_strerror",
+    "cc_get_timing", "cc_reset_timing", "cc_count_cycle_noalloc", "cc_count_batch", "cc_set_graph_capture",
+    "cc_autotune", "cc_strerror",
 ]
+
+
+class cc_request(ctypes.Structure):
+    _fields_ = [("graph_id", ctypes.c_int32), ("query_id", ctypes.c_int32), ("first_trial", ctypes.c_int32),
+                ("trials", ctypes.c_int32)]
 
 _lib = None
 
@@ -89,6 +95,10 @@ def lib():
             "cc_get_timing": ([P, ctypes.c_char_p, DP, I64P, ctypes.c_int], ctypes.c_int),
             "cc_reset_timing": ([P], ctypes.c_int),
             "cc_count_cycle_noalloc": ([ctypes.c_int, P, ctypes.c_int, I64, P, P, P, U64P], ctypes.c_int),
+            "cc_count_batch": ([P, ctypes.POINTER(cc_request), ctypes.c_int, U64P, ctypes.POINTER(ctypes.c_int)],
+                               ctypes.c_int),
+            "cc_set_graph_capture": ([P, ctypes.c_int], ctypes.c_int),
+            "cc_autotune": ([P, I32, I32, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "cc_strerror": ([ctypes.c_int], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -291,6 +301,31 @@ def cc_count_cycle_noalloc(device: int, stream: int | None, L: int, n: int, d_ro
                                         ctypes.c_void_p(d_col), ctypes.c_void_p(d_colors), ctypes.byref(out)),
            "cc_count_cycle_noalloc")
     return out.value
+
+
+def cc_count_batch(h, requests):
+    """requests: list of (graph_id, query_id, first_trial, trials).
+    Returns (list of uint64 arrays, one per request; list of status codes)."""
+    reqs = (cc_request * len(requests))(*[cc_request(*r) for r in requests])
+    total = sum(r[3] for r in requests)
+    out = np.zeros(max(total, 1), dtype=np.uint64)
+    st = (ctypes.c_int * len(requests))()
+    _check(lib().cc_count_batch(h, reqs, len(requests), _ptr(out, ctypes.c_uint64), st), "cc_count_batch")
+    res, i = [], 0
+    for r in requests:
+        res.append(out[i:i + r[3]].copy())
+        i += r[3]
+    return res, [int(x) for x in st]
+
+
+def cc_set_graph_capture(h, enable: bool) -> None:
+    _check(lib().cc_set_graph_capture(h, 1 if enable else 0), "cc_set_graph_capture")
+
+
+def cc_autotune(h, gid: int, qid: int) -> int:
+    hd = ctypes.c_int(0)
+    _check(lib().cc_autotune(h, gid, qid, ctypes.byref(hd)), "cc_autotune")
+    return hd.value
 
 
 def cc_strerror(code: int) -> str:

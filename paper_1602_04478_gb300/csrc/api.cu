@@ -13,10 +13,6 @@
 
 #include "cc_kernels.h"
 
-struct cc_ctx {
-  cc::Ctx c;
-};
-
 namespace cc {
 
 void *dev_alloc(Ctx &c, size_t bytes) {
@@ -56,6 +52,24 @@ int ensure_scratch(Ctx &c, size_t bytes) {
   return CC_OK;
 }
 
+int ensure_hv_scratch(Ctx &c, size_t bytes) {
+  if (c.hv_scratch_bytes < bytes) {
+    if (c.hv_scratch) {
+      cudaStreamSynchronize(c.stream);
+      dev_free(c, c.hv_scratch, c.hv_scratch_bytes);
+    }
+    c.hv_scratch = dev_alloc(c, bytes);
+    c.hv_scratch_bytes = c.hv_scratch ? bytes : 0;
+    if (!c.hv_scratch) return CC_ERR_OOM;
+    c.hv_dirty = true;
+  }
+  if (c.hv_dirty) {
+    if (cudaMemsetAsync(c.hv_scratch, 0, c.hv_scratch_bytes, c.stream) != cudaSuccess) return CC_ERR_CUDA;
+    c.hv_dirty = false;
+  }
+  return CC_OK;
+}
+
 void timing_begin(Ctx &c, const char *name) {
   if (!c.timing) return;
   cudaEvent_t a, b;
@@ -87,12 +101,6 @@ void timing_flush(Ctx &c) {
 
 namespace {
 
-struct Table {
-  u64 *p = nullptr;
-  size_t bytes = 0;
-  int arity = 0;  // 1 unary, 2 edge-keyed
-  int s = 0, R = 0;
-};
 
 TabU tab_u(const std::vector<Table> &T, int idx) {
   TabU t;
@@ -141,52 +149,63 @@ size_t plan_table_bytes(const Plan &p, const DevGraph &g) {
   return total;
 }
 
-// One colouring pass of the plan.  d_per_vertex (rank order, nullable)
-// receives the root's split by vertex.
-int run_plan(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, u64 *count, bool *overflow,
-             u64 *d_per_vertex, double *units = nullptr) {
-  const int k = p.k;
-  if (c.budget && c.in_use + plan_table_bytes(p, g) + (size_t)g.n > c.budget) return CC_ERR_OOM;
-  uint8_t *d_col = (uint8_t *)dev_alloc(c, (size_t)g.n);
-  if (!d_col) return CC_ERR_OOM;
-  int *d_counter = (int *)dev_alloc(c, 256);
-  std::vector<Table> T(p.stages.size());
-  int rc = CC_OK;
-  auto release = [&]() {
-    cudaStreamSynchronize(c.stream);
-    for (auto &t : T) dev_free(c, t.p, t.bytes);
-    dev_free(c, d_col, (size_t)g.n);
-    dev_free(c, d_counter, 256);
-  };
-  if (!d_counter) { release(); return CC_ERR_OOM; }
-  if ((rc = check(cudaMemsetAsync(c.d_status, 0, 8 * sizeof(u64), c.stream))) != CC_OK) { release(); return rc; }
-  double host_units = 0.0;
-  if ((rc = colors_fill(c, g, k, trial, d_col)) != CC_OK) { release(); return rc; }
-  if (d_per_vertex && (rc = check(cudaMemsetAsync(d_per_vertex, 0, (size_t)g.n * 8, c.stream))) != CC_OK) {
-    release();
-    return rc;
+}  // namespace
+
+// Device buffers of one colouring pass (PassBuffers): a table per block, the
+// colours and the triangle work counter.
+int alloc_pass(Ctx &c, const DevGraph &g, const Plan &p, PassBuffers &B) {
+  if (c.budget && c.in_use + plan_table_bytes(p, g) + (size_t)g.n + 256 > c.budget) return CC_ERR_OOM;
+  B.T.assign(p.stages.size(), Table());
+  B.colors = (uint8_t *)dev_alloc(c, (size_t)g.n);
+  B.counter = (int *)dev_alloc(c, 256);
+  if (!B.colors || !B.counter) return CC_ERR_OOM;
+  for (size_t i = 0; i < p.stages.size(); i++) {
+    int R = 0, ar = 0;
+    size_t bytes = table_bytes(p, p.stages[i], g, &R, &ar);
+    if (!bytes) continue;
+    B.T[i].p = (u64 *)dev_alloc(c, bytes);
+    if (!B.T[i].p) return CC_ERR_OOM;
+    B.T[i].bytes = bytes;
+    B.T[i].arity = ar;
+    B.T[i].s = p.stages[i].s;
+    B.T[i].R = R;
   }
+  return CC_OK;
+}
+
+void free_pass(Ctx &c, const DevGraph &g, PassBuffers &B) {
+  for (auto &t : B.T) dev_free(c, t.p, t.bytes);
+  B.T.clear();
+  dev_free(c, B.colors, (size_t)g.n);
+  dev_free(c, B.counter, 256);
+  B.colors = nullptr;
+  B.counter = nullptr;
+}
+
+// Issue one colouring pass of the plan on the context's stream: status words
+// zeroed, colours, every block bottom-up into its table, the root into
+// status[ST_COUNT] (and d_per_vertex, rank order, when given).  No host
+// synchronisation, so a sequence of passes can be captured in a CUDA graph.
+int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers &B, u64 *status,
+                 u64 *d_per_vertex, bool count_units, double *host_units) {
+  const int k = p.k;
+  int rc = CC_OK;
+  if ((rc = check(cudaMemsetAsync(status, 0, 8 * sizeof(u64), c.stream))) != CC_OK) return rc;
+  if ((rc = colors_fill(c, g, k, trial, B.colors)) != CC_OK) return rc;
+  if (d_per_vertex && (rc = check(cudaMemsetAsync(d_per_vertex, 0, (size_t)g.n * 8, c.stream))) != CC_OK) return rc;
   Lut lut{c.lut_rank, c.lut_unrank};
   GraphView gv = view_of(g);
   c.cur_graph_row = g.h_row.data();
+  std::vector<Table> &T = B.T;
   for (size_t i = 0; i < p.stages.size() && rc == CC_OK; i++) {
     const Stage &st = p.stages[i];
     bool is_root = i + 1 == p.stages.size();
-    int R = 0, ar = 0;
-    size_t bytes = table_bytes(p, st, g, &R, &ar);
-    if (bytes) {
-      T[i].p = (u64 *)dev_alloc(c, bytes);
-      if (!T[i].p) { rc = CC_ERR_OOM; break; }
-      T[i].bytes = bytes;
-      T[i].arity = ar;
-      T[i].s = st.s;
-      T[i].R = R;
-      if ((rc = check(cudaMemsetAsync(T[i].p, 0, bytes, c.stream))) != CC_OK) break;
-    }
+    const int R = T[i].R;
+    if (T[i].p && (rc = check(cudaMemsetAsync(T[i].p, 0, T[i].bytes, c.stream))) != CC_OK) break;
     if (st.kind == ST_LEAF) {
       LeafArgs a;
       a.g = gv;
-      a.colors = d_col;
+      a.colors = B.colors;
       a.k = k;
       a.lut = lut;
       a.A = tab_u(T, st.node_child[0]);
@@ -198,15 +217,15 @@ int run_plan(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, u64 *count, bool
       a.out = T[i].p;
       a.s_out = st.s;
       a.R_out = R;
-      a.status = c.d_status;
+      a.status = status;
       if (sA + a.sY - 1 != st.s) { rc = CC_ERR_INVALID_ARG; break; }
       // every directed edge joins one edge row with one row of the leaf's block
-      host_units += (double)g.nnz * (a.E.p ? a.E.R : 1) * (a.B.p ? a.B.R : 1);
+      if (host_units) *host_units += (double)g.nnz * (a.E.p ? a.E.R : 1) * (a.B.p ? a.B.R : 1);
       rc = launch_leaf(c, a);
     } else if (st.kind == ST_TRI) {
       TriArgs a;
       a.g = gv;
-      a.colors = d_col;
+      a.colors = B.colors;
       a.k = k;
       a.lut = lut;
       for (int j = 0; j < 3; j++) {
@@ -221,14 +240,14 @@ int run_plan(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, u64 *count, bool
       a.R_out = R;
       a.out = T[i].p;
       a.per_vertex = is_root ? d_per_vertex : nullptr;
-      a.status = c.d_status;
-      a.work_counter = d_counter;
-      a.count_units = units != nullptr;
+      a.status = status;
+      a.work_counter = B.counter;
+      a.count_units = count_units;
       rc = launch_triangle(c, a);
     } else if (st.kind == ST_CYCLE_ROOT) {
       CycleArgs a;
       a.g = gv;
-      a.colors = d_col;
+      a.colors = B.colors;
       a.k = k;
       a.lut = lut;
       a.L = st.L;
@@ -249,52 +268,52 @@ int run_plan(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, u64 *count, bool
         a.multiplier = 1;
       }
       a.per_vertex = d_per_vertex;
-      a.status = c.d_status;
-      a.count_units = units != nullptr;
+      a.status = status;
+      a.count_units = count_units;
       rc = launch_cycle(c, a);
-      if (rc != CC_OK) c.scratch_dirty = true;
+      if (rc != CC_OK) c.scratch_dirty = c.hv_dirty = true;
     } else if (st.kind == ST_ROOT_NODE) {
       const Table &ct = T[st.node_child[0]];
       if (ct.R != 1) { rc = CC_ERR_INVALID_ARG; break; }
-      rc = launch_root_sum(c, gv, ct.p, d_per_vertex, c.d_status);
+      rc = launch_root_sum(c, gv, ct.p, d_per_vertex, status);
     } else {
       rc = CC_ERR_UNSUPPORTED;
     }
-    // children's tables are no longer needed
-    if (rc == CC_OK) {
-      int nchild = st.kind == ST_ROOT_NODE ? 1 : st.L;
-      std::vector<int> kids;
-      for (int j = 0; j < nchild; j++) {
-        if (st.node_child[j] >= 0) kids.push_back(st.node_child[j]);
-        if (st.edge_child[j] >= 0) kids.push_back(st.edge_child[j]);
-      }
-      if (!kids.empty()) {
-        cudaStreamSynchronize(c.stream);
-        for (int kid : kids) {
-          dev_free(c, T[kid].p, T[kid].bytes);
-          T[kid].p = nullptr;
-          T[kid].bytes = 0;
-        }
-      }
-    }
   }
+  return rc;
+}
+
+int status_code(const u64 *st) {
+  if (st[ST_TIMEOUT] & 1ull) return CC_ERR_TIMEOUT;
+  if (st[ST_TIMEOUT] & 2ull) return CC_ERR_UNSUPPORTED;
+  if (st[ST_OVERFLOW]) return CC_ERR_OVERFLOW;
+  return CC_OK;
+}
+
+// One colouring pass (plain form): allocate, enqueue, wait, read the status.
+int run_plan(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, u64 *count, bool *overflow,
+             u64 *d_per_vertex, double *units) {
+  PassBuffers B;
+  int rc = alloc_pass(c, g, p, B);
+  double host_units = 0.0;
+  if (rc == CC_OK) rc = enqueue_pass(c, g, p, trial, B, c.d_status, d_per_vertex, units != nullptr, &host_units);
   u64 status[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (rc == CC_OK) {
     rc = check(cudaMemcpyAsync(status, c.d_status, sizeof(status), cudaMemcpyDeviceToHost, c.stream));
     if (rc == CC_OK) rc = check(cudaStreamSynchronize(c.stream));
   }
   timing_flush(c);
-  release();
+  cudaStreamSynchronize(c.stream);
+  free_pass(c, g, B);
   if (rc != CC_OK) return rc;
-  if (status[ST_TIMEOUT] & 1ull) return CC_ERR_TIMEOUT;
-  if (status[ST_TIMEOUT] & 2ull) return CC_ERR_UNSUPPORTED;
+  int sc = status_code(status);
+  if (sc != CC_OK && sc != CC_ERR_OVERFLOW) return sc;
   *count = status[ST_COUNT];
-  *overflow = status[ST_OVERFLOW] != 0;
+  *overflow = sc == CC_ERR_OVERFLOW;
   if (units) *units = host_units + (double)status[ST_UNITS];
   return CC_OK;
 }
 
-}  // namespace
 }  // namespace cc
 
 using namespace cc;
@@ -343,6 +362,8 @@ void cc_destroy(cc_ctx *ctx) {
   for (auto &g : c.graphs) graph_free(c, g.second);
   dev_free(c, c.scratch, c.scratch_bytes);
   dev_free(c, c.hv_scratch, c.hv_scratch_bytes);
+  batch_cache_clear(c);
+  if (c.own_stream) cudaStreamDestroy(c.own_stream);
   dev_free(c, c.lut_rank, 4096 * 2);
   dev_free(c, c.lut_unrank, 13 * kUnrankStride * 2);
   dev_free(c, c.d_status, 64);
@@ -368,6 +389,7 @@ int cc_set_allocator(cc_ctx *ctx, cc_alloc_fn alloc, cc_free_fn free_fn, void *u
 
 int cc_set_heavy_degree(cc_ctx *ctx, int degree) {
   if (!ctx || degree < -1) return CC_ERR_INVALID_ARG;
+  if (ctx->c.heavy_degree != degree) batch_cache_clear(ctx->c);
   ctx->c.heavy_degree = degree;
   return CC_OK;
 }
@@ -397,6 +419,7 @@ int cc_free_graph(cc_ctx *ctx, int32_t graph_id) {
   auto it = ctx->c.graphs.find(graph_id);
   if (it == ctx->c.graphs.end()) return CC_ERR_INVALID_ARG;
   cudaStreamSynchronize(ctx->c.stream);
+  batch_cache_clear(ctx->c);  // cached batches may point into this graph
   graph_free(ctx->c, it->second);
   ctx->c.graphs.erase(it);
   return CC_OK;
@@ -426,6 +449,7 @@ int cc_set_query(cc_ctx *ctx, int k, int n_edges, const int32_t *edges, int32_t 
 }
 
 int cc_set_decomposition(cc_ctx *ctx, int32_t query_id, const int32_t *block_seq, int len) {
+  if (ctx) batch_cache_clear(ctx->c);
   if (!ctx || len < 0 || (len > 0 && !block_seq)) return CC_ERR_INVALID_ARG;
   auto it = ctx->c.plans.find(query_id);
   if (it == ctx->c.plans.end()) return CC_ERR_INVALID_ARG;
@@ -488,12 +512,14 @@ int cc_query_info(cc_ctx *ctx, int32_t query_id, int *k, int64_t *aut, int *n_bl
 
 int cc_set_coloring_seed(cc_ctx *ctx, uint64_t seed) {
   if (!ctx) return CC_ERR_INVALID_ARG;
+  if (ctx->c.seed != seed) batch_cache_clear(ctx->c);  // the seed is baked into captured launches
   ctx->c.seed = seed;
   return CC_OK;
 }
 
 int cc_set_colors(cc_ctx *ctx, int32_t graph_id, const uint8_t *colors, int T) {
   if (!ctx || !colors || T <= 0) return CC_ERR_INVALID_ARG;
+  batch_cache_clear(ctx->c);
   auto it = ctx->c.graphs.find(graph_id);
   if (it == ctx->c.graphs.end()) return CC_ERR_INVALID_ARG;
   int mx = 0;
@@ -506,6 +532,7 @@ int cc_set_colors(cc_ctx *ctx, int32_t graph_id, const uint8_t *colors, int T) {
 
 int cc_clear_colors(cc_ctx *ctx, int32_t graph_id) {
   if (!ctx) return CC_ERR_INVALID_ARG;
+  batch_cache_clear(ctx->c);
   auto it = ctx->c.graphs.find(graph_id);
   if (it == ctx->c.graphs.end()) return CC_ERR_INVALID_ARG;
   return colors_set(ctx->c, it->second, nullptr, 0);
@@ -539,7 +566,8 @@ int cc_count(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int first_trial, i
   for (int t = 0; t < T; t++) {
     u64 cnt = 0;
     bool ovf = false;
-    rc = run_plan(c, *g, *p, (int64_t)first_trial + t, &cnt, &ovf, nullptr);
+    c.cur_tuned_heavy = g->tuned_heavy.count(query_id) ? g->tuned_heavy[query_id] : -1;
+    rc = run_plan(c, *g, *p, (int64_t)first_trial + t, &cnt, &ovf, nullptr, nullptr);
     if (rc != CC_OK) return rc;
     if (ovf) {
       colorful[t] = UINT64_MAX;
@@ -566,7 +594,8 @@ int cc_count_per_vertex(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int tri
   if (!d_pv) return CC_ERR_OOM;
   u64 cnt = 0;
   bool ovf = false;
-  rc = run_plan(c, *g, *p, trial, &cnt, &ovf, d_pv);
+  c.cur_tuned_heavy = g->tuned_heavy.count(query_id) ? g->tuned_heavy[query_id] : -1;
+  rc = run_plan(c, *g, *p, trial, &cnt, &ovf, d_pv, nullptr);
   if (rc == CC_OK) {
     std::vector<u64> by_rank(g->n);
     std::vector<int32_t> id_of(g->n);

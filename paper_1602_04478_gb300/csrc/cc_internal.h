@@ -61,6 +61,7 @@ struct DevGraph {
   int colors_max = -1;        // largest explicit colour (must be below the query's k)
   std::vector<int64_t> h_row;  // host copy of the relabelled row pointers
   std::map<int, double> work_cache;  // query id -> structural work units
+  std::map<int, int> tuned_heavy;    // query id -> heavy-source degree threshold (autotuned)
 };
 
 // -------------------------------- context --------------------------------
@@ -84,11 +85,16 @@ struct Ctx {
   uint64_t scratch_layout = 0;   // layout of the cycle kernel's scratch last used
   bool scratch_dirty = true;     // contents unknown (fresh, or a launch failed)
   unsigned epoch = 0;
-  void *hv_scratch = nullptr;    // heavy-source cycle scratch
+  void *hv_scratch = nullptr;    // heavy-source cycle scratch (all zero between launches)
   size_t hv_scratch_bytes = 0;
-  uint64_t hv_layout = 0;
+  bool hv_dirty = true;
   const int64_t *cur_graph_row = nullptr;  // host row pointers of the graph being counted
-  int heavy_degree = -1;         // sources of at least this degree take the heavy path (-1: default)
+  int heavy_degree = -1;         // sources of at least this degree take the heavy path (-1: tuned / default)
+  int cur_tuned_heavy = -1;      // tuned threshold of the (graph, query) being enqueued, -1 none
+  cudaStream_t own_stream = nullptr;  // created for graph capture when the caller's stream is the legacy one
+  bool capture = true;           // batches replay a captured CUDA graph
+  struct BatchCache;
+  std::map<std::string, BatchCache *> batches;
   // timing
   bool timing = false;
   std::map<std::string, std::pair<double, int64_t>> times;
@@ -98,10 +104,17 @@ struct Ctx {
 void *dev_alloc(Ctx &c, size_t bytes);
 void dev_free(Ctx &c, void *p, size_t bytes);
 int ensure_scratch(Ctx &c, size_t bytes);
+int ensure_hv_scratch(Ctx &c, size_t bytes);  // grows and, when fresh or dirty, zeroes the heavy scratch
 
 // kernel-launch bracketing for the optional timing
+void batch_cache_clear(Ctx &c);  // drop captured batch graphs and their buffers
 void timing_begin(Ctx &c, const char *name);
 void timing_end(Ctx &c);
 void timing_flush(Ctx &c);
 
 }  // namespace cc
+
+// the opaque handle of the C-ABI
+struct cc_ctx {
+  cc::Ctx c;
+};

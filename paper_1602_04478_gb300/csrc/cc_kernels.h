@@ -99,6 +99,26 @@ int heavy_group_size(const CycleArgs &a);
 int launch_cycle(Ctx &c, const CycleArgs &a);
 size_t cycle_scratch_bytes(const CycleArgs &a, int slots);
 
+// executor (api.cu)
+struct Table {
+  u64 *p = nullptr;
+  size_t bytes = 0;
+  int arity = 0;  // 1 unary, 2 edge-keyed
+  int s = 0, R = 0;
+};
+struct PassBuffers {
+  std::vector<Table> T;
+  uint8_t *colors = nullptr;
+  int *counter = nullptr;
+};
+int alloc_pass(Ctx &c, const DevGraph &g, const Plan &p, PassBuffers &B);
+void free_pass(Ctx &c, const DevGraph &g, PassBuffers &B);
+int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers &B, u64 *status, u64 *d_per_vertex,
+                 bool count_units, double *host_units);
+int status_code(const u64 *st);
+int run_plan(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, u64 *count, bool *overflow, u64 *d_per_vertex,
+             double *units);
+
 int graph_load(Ctx &c, int64_t n, const int64_t *row_ptr, const int32_t *col, int64_t nnz, DevGraph &g);
 void graph_free(Ctx &c, DevGraph &g);
 int colors_fill(Ctx &c, const DevGraph &g, int k, int64_t trial, uint8_t *d_out);

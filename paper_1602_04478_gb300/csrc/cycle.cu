@@ -226,8 +226,8 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
     if (du >= 2) {
       for (int hi = 0; hi < a.n_h; hi++) {
         const int h = a.hs[hi];
-        const unsigned long long cur =
-            ((unsigned long long)(sc.epoch & 0xFFFFu) << 32) | ((unsigned long long)(u + 1) << 3) | (unsigned)hi;
+        // stamps are cleared after every (source, h), so (u, h) is a unique key
+        const unsigned long long cur = ((unsigned long long)(u + 1) << 3) | (unsigned)hi;
         // levels each half materialises; with a shared chain half 0 carries both
         int mat[2] = {rp - 1, rm - 1};
         if (sc.shared_chain) {
@@ -456,21 +456,27 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
           }
         }
         __syncthreads();
-        // ---- clear the rows this source touched ----
+        // ---- clear the rows and stamps this source touched (scratch returns to zero) ----
         for (int hf = 0; hf < 2; hf++)
           for (int j = 1; j <= mat[hf]; j++) {
             const int cnt = s_cnt[hf * kMaxLevels + j];
             const int rs = sc.rstride[hf][j], ps = sc.pstride[hf][j];
             for (int i = tid; i < cnt; i += kCtaThreads) {
               int32_t w = P.list[hf][j][i];
+              P.list[hf][j][i] = 0;
               u64 *r = P.rows[hf][j] + (int64_t)w * rs;
               for (int t = 0; t < rs; t++) r[t] = 0;
               if (ps) {
                 u64 *q = P.pre[hf][j] + (int64_t)w * ps;
                 for (int t = 0; t < ps; t++) q[t] = 0;
               }
+              P.stamp[w] = 0;
             }
           }
+        for (int i = tid; i < s_cnt[2 * kMaxLevels]; i += kCtaThreads) {
+          P.stamp[P.xlist[i]] = 0;
+          P.xlist[i] = 0;
+        }
         __syncthreads();
       }
     }
@@ -551,7 +557,7 @@ int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   CycleArgs a = a_in;
   // sources of degree >= heavy_degree go to the grouped heavy path
   const int64_t n = a.g.n;
-  int hd = c.heavy_degree >= 0 ? c.heavy_degree : 256;
+  int hd = c.heavy_degree >= 0 ? c.heavy_degree : (c.cur_tuned_heavy >= 0 ? c.cur_tuned_heavy : 256);
   if (a.count_units) hd = 1 << 30;  // structural counting runs on the per-CTA path only
   int64_t lo = 0, hi = n;
   while (lo < hi) {
@@ -585,20 +591,21 @@ int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   int *counter = (int *)((char *)c.scratch + (size_t)slots * per);
   // rows are cleared by the kernel after each source; a new layout (or a
   // fresh buffer) starts from zeros, and stamp keys carry the launch number
-  uint64_t layout = (uint64_t)per * 1000003ull + (uint64_t)slots;
-  if (c.scratch_layout != layout || c.scratch_dirty) {
-    if (cudaMemsetAsync(c.scratch, 0, need, c.stream) != cudaSuccess) return CC_ERR_CUDA;
-    c.scratch_layout = layout;
+  // every kernel on this scratch returns it to zero, so only a fresh (or
+  // failed) buffer needs clearing, whatever layout the previous launch used
+  if (c.scratch_dirty) {
+    if (cudaMemsetAsync(c.scratch, 0, c.scratch_bytes, c.stream) != cudaSuccess) return CC_ERR_CUDA;
     c.scratch_dirty = false;
-  } else if (cudaMemsetAsync(counter, 0, sizeof(int), c.stream) != cudaSuccess) {
-    return CC_ERR_CUDA;
   }
-  sc.epoch = ++c.epoch;
+  if (cudaMemsetAsync(counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
+  sc.epoch = 0;
   size_t smem = (size_t)kWarps * 2 * sc.acc_stride * sizeof(u64);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   timing_begin(c, "cycle_closure");
   k_cycle<<<slots, kCtaThreads, smem, c.stream>>>(a, sc, counter);
   timing_end(c);
+  // the queue counter returns to zero too: the whole scratch is zero between launches
+  if (cudaMemsetAsync(counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
   return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }
 

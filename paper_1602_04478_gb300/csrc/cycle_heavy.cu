@@ -455,6 +455,7 @@ __global__ void k_hv_clear(CycleArgs a, HvScratch S, HvGroup G) {
         const int rs = S.rstride[hf][j], ps = S.pstride[hf][j];
         for (int64_t i = t0; i < cnt; i += nt) {
           const int32_t w = S.list[hf][j][(int64_t)b * n + i];
+          S.list[hf][j][(int64_t)b * n + i] = 0;
           u64 *r = S.rows[hf][j] + ((int64_t)b * n + w) * rs;
           for (int q = 0; q < rs; q++) r[q] = 0;
           if (ps) {
@@ -462,6 +463,7 @@ __global__ void k_hv_clear(CycleArgs a, HvScratch S, HvGroup G) {
             for (int q = 0; q < ps; q++) p[q] = 0;
           }
           S.member[w] = 0;
+          S.stamp[(int64_t)b * n + w] = 0;
         }
       }
 }
@@ -558,20 +560,9 @@ int run_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank, int B) {
   size_t o_member = take((size_t)n * 4);
   size_t o_tot = take(2 * kHvMaxB * 8);
   size_t need = off;
-  if (c.hv_scratch_bytes < need) {
-    cudaStreamSynchronize(c.stream);
-    dev_free(c, c.hv_scratch, c.hv_scratch_bytes);
-    c.hv_scratch = dev_alloc(c, need);
-    c.hv_scratch_bytes = c.hv_scratch ? need : 0;
-    if (!c.hv_scratch) return CC_ERR_OOM;
-    c.hv_layout = 0;
-  }
+  int rc0 = ensure_hv_scratch(c, need);
+  if (rc0 != CC_OK) return rc0;
   char *base = (char *)c.hv_scratch;
-  uint64_t layout = need * 31 + (uint64_t)B;
-  if (c.hv_layout != layout) {
-    if (cudaMemsetAsync(base, 0, need, c.stream) != cudaSuccess) return CC_ERR_CUDA;
-    c.hv_layout = layout;
-  }
   for (int hf = 0; hf < 2; hf++)
     for (int l = 0; l < kHvLevels; l++) {
       S.rows[hf][l] = (u64 *)(base + o_rows[hf][l]);
@@ -604,9 +595,8 @@ int run_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank, int B) {
     for (int b = 0; b < G.B; b++) G.u[b] = (int32_t)(top - b);
     for (int hi = 0; hi < a.n_h; hi++) {
       const int h = a.hs[hi];
-      unsigned ep = ++c.epoch;
-      for (int b = 0; b < G.B; b++)
-        G.key[b] = ((unsigned long long)(ep & 0xFFFFu) << 32) | ((unsigned long long)(G.u[b] + 1) << 3) | hi;
+      // stamps are cleared with the rows after every group and h: (u, h) is a unique key
+      for (int b = 0; b < G.B; b++) G.key[b] = ((unsigned long long)(G.u[b] + 1) << 3) | hi;
       if (cudaMemsetAsync(S.cnt, 0, 2 * kHvLevels * kHvMaxB * sizeof(int), c.stream) != cudaSuccess)
         return CC_ERR_CUDA;
       dim3 g1(std::max<int64_t>(1, std::min<int64_t>(64, (c.cur_graph_row[top + 1] - c.cur_graph_row[top] + 255) / 256)),
@@ -629,6 +619,8 @@ int run_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank, int B) {
       k_hv_finish<<<1, 32, 0, c.stream>>>(a, S, G, hi == a.n_h - 1);
     }
   }
+  // leave the level counts at zero as well: the scratch is all zero between launches
+  if (cudaMemsetAsync(S.cnt, 0, 2 * kHvLevels * kHvMaxB * sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
   return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }
 

@@ -243,6 +243,7 @@ __global__ void k_pc_clear(GraphView g, const uint8_t *colors, PcScratch S, PcGr
       const int cnt = S.cnt[b];
       for (int64_t i = t0; i < cnt; i += nt) {
         const int32_t w = S.list[(int64_t)b * n + i];
+        S.list[(int64_t)b * n + i] = 0;
         S.member[w] = 0;
         *(uint4 *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8) = make_uint4(0, 0, 0, 0);
       }
@@ -361,6 +362,7 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
       u64 mine = 0;
       for (int i = tid; i < nx; i += kPlThreads) {
         const int32_t x = LX[i];
+        if (L >= 5) L3[i] = 0;  // lists are cleared as they are consumed
         const int cx = colors[x];
         const uint32_t fm = ((1u << k) - 1u) & ~((1u << cu) | (1u << cx));
         int f[4];
@@ -401,6 +403,7 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
       __syncthreads();
       for (int i = tid; i < n2; i += kPlThreads) {
         const int32_t w = L2[i];
+        L2[i] = 0;
         uint4 *z = (uint4 *)(W2 + (int64_t)w * 8);
         z[0] = z[1] = make_uint4(0, 0, 0, 0);
         atomicAnd(mark + w, ~1u);
@@ -459,14 +462,11 @@ int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank) {
   if (rc != CC_OK) return rc;
   S.base = (char *)c.scratch;
   int *work = (int *)((char *)c.scratch + (size_t)slots * S.slot_bytes);
-  uint64_t layout = (uint64_t)S.slot_bytes * 1000003ull + (uint64_t)slots * 7 + 3;
-  if (c.scratch_layout != layout || c.scratch_dirty) {
-    if (cudaMemsetAsync(c.scratch, 0, need, c.stream) != cudaSuccess) return CC_ERR_CUDA;
-    c.scratch_layout = layout;
+  if (c.scratch_dirty) {
+    if (cudaMemsetAsync(c.scratch, 0, c.scratch_bytes, c.stream) != cudaSuccess) return CC_ERR_CUDA;
     c.scratch_dirty = false;
-  } else if (cudaMemsetAsync(work, 0, sizeof(int), c.stream) != cudaSuccess) {
-    return CC_ERR_CUDA;
   }
+  if (cudaMemsetAsync(work, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
   timing_begin(c, "cycle_plain_light");
   if (a.L == 4)
     k_pc_light<4><<<slots, kPlThreads, 0, c.stream>>>(a.g, a.colors, S, end_rank, work, a.multiplier,
@@ -478,6 +478,8 @@ int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank) {
     k_pc_light<6><<<slots, kPlThreads, 0, c.stream>>>(a.g, a.colors, S, end_rank, work, a.multiplier,
                                                        a.per_vertex, a.status, a.k);
   timing_end(c);
+  // the queue counter returns to zero too: the whole scratch is zero between launches
+  if (cudaMemsetAsync(work, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
   return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }
 
@@ -528,20 +530,9 @@ int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank) {
   size_t o_cnt = take(kPcMaxB * 4);
   size_t o_tot = take(kPcMaxB * 8);
   size_t need = off;
-  if (c.hv_scratch_bytes < need) {
-    cudaStreamSynchronize(c.stream);
-    dev_free(c, c.hv_scratch, c.hv_scratch_bytes);
-    c.hv_scratch = dev_alloc(c, need);
-    c.hv_scratch_bytes = c.hv_scratch ? need : 0;
-    if (!c.hv_scratch) return CC_ERR_OOM;
-    c.hv_layout = 0;
-  }
+  int rc0 = ensure_hv_scratch(c, need);
+  if (rc0 != CC_OK) return rc0;
   char *base = (char *)c.hv_scratch;
-  uint64_t layout = need * 37 + 7 + (uint64_t)a.L;
-  if (c.hv_layout != layout) {
-    if (cudaMemsetAsync(base, 0, need, c.stream) != cudaSuccess) return CC_ERR_CUDA;
-    c.hv_layout = layout;
-  }
   PcScratch S;
   S.w2 = (uint16_t *)(base + o_w2);
   S.member = (unsigned long long *)(base + o_mem);

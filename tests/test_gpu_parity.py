@@ -317,3 +317,47 @@ def test_memory_budget_oom(cc):
         assert got == int(ctx.count(gid, qid)[0][0])
     finally:
         ctx.close()
+
+
+# ------------------------------ batched form ------------------------------
+@pytest.mark.parametrize("capture", [True, False])
+def test_batch_equals_plain(cc, capture):
+    import paper_1602_04478_gb300 as P
+    g1, g2 = graph("cl3000"), graph("er2000")
+    a, b = cc.load_graph(g1), cc.load_graph(g2)
+    try:
+        P.cc_set_graph_capture(cc.h, capture)
+        P.cc_set_coloring_seed(cc.h, 3)
+        qs = {name: cc.set_query(*QUERIES[name]) for name in ["C5", "chord_pendant", "glasses", "C6", "C4"]}
+        reqs = [(a, qs["C5"], 0, 4), (a, qs["chord_pendant"], 2, 3), (b, qs["glasses"], 0, 2),
+                (b, qs["C6"], 5, 2), (a, qs["C4"], 1, 1)]
+        for rep in range(3):  # first call runs eagerly and records; later calls replay
+            res, st = P.cc_count_batch(cc.h, reqs)
+            assert st == [0] * len(reqs)
+            for (gid, qid, t0, T), got in zip(reqs, res):
+                want = cc.count(gid, qid, t0, T)[0]
+                assert [int(x) for x in got] == [int(x) for x in want], (rep, gid, qid)
+        # oracle spot check of one request
+        k, e = QUERIES["C5"]
+        assert int(res[0][1]) == O.dp_count(g1, k, e, O.colors(3, 1, g1.n, k))[0]
+    finally:
+        P.cc_set_graph_capture(cc.h, True)
+        cc.free_graph(a)
+        cc.free_graph(b)
+
+
+def test_autotune_keeps_counts(cc):
+    import paper_1602_04478_gb300 as P
+    g = graph("cl3000")
+    gid = cc.load_graph(g)
+    try:
+        P.cc_set_coloring_seed(cc.h, 8)
+        qid = cc.set_query(*QUERIES["C6"])
+        before = [int(x) for x in cc.count(gid, qid, 0, 2)[0]]
+        hd = P.cc_autotune(cc.h, gid, qid)
+        assert hd in (64, 128, 256, 512, 1024, 2048, 4096)
+        assert [int(x) for x in cc.count(gid, qid, 0, 2)[0]] == before
+        res, _ = P.cc_count_batch(cc.h, [(gid, qid, 0, 2)])
+        assert [int(x) for x in res[0]] == before
+    finally:
+        cc.free_graph(gid)
