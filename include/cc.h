@@ -173,6 +173,39 @@ int cc_set_graph_capture(cc_ctx *ctx, int enable);
  * (nullable) receives the choice. */
 int cc_autotune(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int *heavy_degree);
 
+/* Serving loop (continuous batching).  A server holds graphs and queries
+ * resident on one device and `workers` worker contexts, each with its own
+ * CUDA stream and scratch.  Requests (graph, query, trials) are submitted at
+ * any time; they are admitted first-in first-out whenever a worker is idle
+ * and the request's table memory (the bytes of its plan's projection tables
+ * on that graph, at most (|V| or |E|) * 2^k * 8 per table) fits in what the
+ * budget has left (0 = no memory limit); admitted requests run concurrently
+ * on the workers' streams and a finished one frees its worker and memory for
+ * the next.  colorful (host, `trials` entries) must stay valid until the
+ * request's result has been polled.  Results carry submit / admit / done
+ * times in seconds since the server was created.  Counts equal cc_count's
+ * for the same graph, query, trials and seed. */
+typedef struct cc_server cc_server;
+typedef struct cc_server_result {
+  int64_t ticket;
+  int32_t status;  /* CC_OK, CC_ERR_OVERFLOW, ... of the request's count */
+  int32_t trials;
+  double submit_s, admit_s, done_s;
+} cc_server_result;
+int cc_server_create(cc_server **out, int device, int workers, size_t memory_budget);
+void cc_server_destroy(cc_server *s);
+int cc_server_load_csr(cc_server *s, int64_t n, const int64_t *row_ptr, const int32_t *col, int64_t nnz,
+                       int32_t *graph_id);
+int cc_server_set_query(cc_server *s, int k, int n_edges, const int32_t *edges, int32_t *query_id);
+int cc_server_set_coloring_seed(cc_server *s, uint64_t seed);
+/* CC_ERR_OOM when the request alone exceeds the memory budget. */
+int cc_server_submit(cc_server *s, int32_t graph_id, int32_t query_id, int first_trial, int trials,
+                     uint64_t *colorful, int64_t *ticket);
+/* Move up to cap finished results to out, waiting up to timeout_ms for one;
+ * returns how many were written. */
+int cc_server_poll(cc_server *s, cc_server_result *out, int cap, int timeout_ms);
+int cc_server_stats(cc_server *s, int64_t *waiting, int64_t *running, size_t *bytes_in_flight);
+
 /* One trial, and the count split by vertex: for a root cycle block the
  * colourful matches whose highest root-cycle vertex (degree order) is v;
  * for a root that is a single node, the matches mapping that node to v.

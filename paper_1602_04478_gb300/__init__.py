@@ -34,8 +34,14 @@ EXPORTED = [
     "cc_graph_info", "cc_set_query", "cc_set_decomposition", "cc_plan_inspect", "cc_query_info", "cc_set_coloring_seed",
     "cc_set_colors", "cc_clear_colors", "cc_count", "cc_count_per_vertex", "cc_work_units", "cc_set_timing",
     "cc_get_timing", "cc_reset_timing", "cc_count_cycle_noalloc", "cc_count_batch", "cc_set_graph_capture",
-    "cc_autotune", "cc_strerror",
+    "cc_autotune", "cc_server_create", "cc_server_destroy", "cc_server_load_csr", "cc_server_set_query",
+    "cc_server_set_coloring_seed", "cc_server_submit", "cc_server_poll", "cc_server_stats", "cc_strerror",
 ]
+
+
+class cc_server_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("status", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
 
 
 class cc_request(ctypes.Structure):
@@ -99,6 +105,14 @@ def lib():
                                ctypes.c_int),
             "cc_set_graph_capture": ([P, ctypes.c_int], ctypes.c_int),
             "cc_autotune": ([P, I32, I32, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+            "cc_server_create": ([ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
+            "cc_server_destroy": ([P], None),
+            "cc_server_load_csr": ([P, I64, I64P, I32P, I64, I32P], ctypes.c_int),
+            "cc_server_set_query": ([P, ctypes.c_int, ctypes.c_int, I32P, I32P], ctypes.c_int),
+            "cc_server_set_coloring_seed": ([P, U64], ctypes.c_int),
+            "cc_server_submit": ([P, I32, I32, ctypes.c_int, ctypes.c_int, U64P, I64P], ctypes.c_int),
+            "cc_server_poll": ([P, ctypes.POINTER(cc_server_result), ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "cc_server_stats": ([P, I64P, I64P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
             "cc_strerror": ([ctypes.c_int], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -326,6 +340,74 @@ def cc_autotune(h, gid: int, qid: int) -> int:
     hd = ctypes.c_int(0)
     _check(lib().cc_autotune(h, gid, qid, ctypes.byref(hd)), "cc_autotune")
     return hd.value
+
+
+class Server:
+    """The library's serving loop (cc_server_*): graphs and queries resident,
+    requests admitted by table memory as workers and memory free up."""
+
+    def __init__(self, device: int = 0, workers: int = 4, memory_budget: int = 0):
+        self.h = ctypes.c_void_p()
+        _check(lib().cc_server_create(ctypes.byref(self.h), device, workers, memory_budget), "cc_server_create")
+        self._bufs = {}
+        self.n_of = {}
+
+    def close(self):
+        if self.h:
+            lib().cc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_graph(self, g) -> int:
+        rp = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
+        cl = np.ascontiguousarray(g.col, dtype=np.int32)
+        if cl.size == 0:
+            cl = np.zeros(1, dtype=np.int32)
+        gid = ctypes.c_int32(0)
+        _check(lib().cc_server_load_csr(self.h, g.n, _ptr(rp, ctypes.c_int64), _ptr(cl, ctypes.c_int32),
+                                        int(rp[-1]), ctypes.byref(gid)), "cc_server_load_csr")
+        self.n_of[gid.value] = g.n
+        return gid.value
+
+    def set_query(self, k: int, edges) -> int:
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        qid = ctypes.c_int32(0)
+        _check(lib().cc_server_set_query(self.h, k, int(e.shape[0]), _ptr(e, ctypes.c_int32), ctypes.byref(qid)),
+               "cc_server_set_query")
+        return qid.value
+
+    def set_seed(self, seed: int) -> None:
+        _check(lib().cc_server_set_coloring_seed(self.h, seed), "cc_server_set_coloring_seed")
+
+    def submit(self, gid: int, qid: int, first_trial: int, trials: int) -> int:
+        buf = np.zeros(trials, dtype=np.uint64)
+        t = ctypes.c_int64(0)
+        _check(lib().cc_server_submit(self.h, gid, qid, first_trial, trials, _ptr(buf, ctypes.c_uint64),
+                                      ctypes.byref(t)), "cc_server_submit")
+        self._bufs[t.value] = buf
+        return t.value
+
+    def poll(self, cap: int = 256, timeout_ms: int = 0):
+        out = (cc_server_result * cap)()
+        n = lib().cc_server_poll(self.h, out, cap, timeout_ms)
+        if n < 0:
+            raise CCError(n, "cc_server_poll")
+        res = []
+        for r in out[:n]:
+            res.append({"ticket": r.ticket, "status": r.status, "trials": r.trials, "submit_s": r.submit_s,
+                        "admit_s": r.admit_s, "done_s": r.done_s, "colorful": self._bufs.pop(r.ticket)})
+        return res
+
+    def stats(self):
+        p, r = ctypes.c_int64(), ctypes.c_int64()
+        b = ctypes.c_size_t()
+        _check(lib().cc_server_stats(self.h, ctypes.byref(p), ctypes.byref(r), ctypes.byref(b)), "cc_server_stats")
+        return {"waiting": p.value, "running": r.value, "bytes_in_flight": b.value}
 
 
 def cc_strerror(code: int) -> str:

@@ -17,7 +17,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libcc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-SOURCES = ["api.cu", "graph.cu", "join.cu", "triangle.cu", "cycle.cu", "cycle_heavy.cu", "cycle_plain.cu", "noalloc.cu", "batch.cu", "plan.cpp"]
+SOURCES = ["api.cu", "graph.cu", "join.cu", "triangle.cu", "cycle.cu", "cycle_heavy.cu", "cycle_plain.cu", "noalloc.cu", "batch.cu", "serve.cu", "plan.cpp"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
          "-I" + os.path.join(ROOT, "include")]
 

@@ -21,7 +21,9 @@ void *dev_alloc(Ctx &c, size_t bytes) {
   void *p = nullptr;
   if (c.alloc) {
     p = c.alloc(bytes, c.alloc_user);
-  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  } else if (cudaMallocAsync(&p, bytes, c.stream) != cudaSuccess) {
+    // stream-ordered: no device-wide synchronisation, so contexts on other
+    // streams keep running while this one allocates
     cudaGetLastError();
     p = nullptr;
   }
@@ -33,7 +35,7 @@ void dev_free(Ctx &c, void *p, size_t bytes) {
   if (!p) return;
   if (bytes == 0) bytes = 16;
   if (c.free_fn) c.free_fn(p, bytes, c.alloc_user);
-  else cudaFree(p);
+  else cudaFreeAsync(p, c.stream);
   c.in_use -= std::min(c.in_use, bytes);
 }
 
@@ -150,6 +152,10 @@ size_t plan_table_bytes(const Plan &p, const DevGraph &g) {
 }
 
 }  // namespace
+
+// Bytes one colouring pass of `p` on `g` holds at its peak: every block's
+// table (all live at once) and the colouring buffer.
+size_t request_table_bytes(const Plan &p, const DevGraph &g) { return plan_table_bytes(p, g) + (size_t)g.n + 256; }
 
 // Device buffers of one colouring pass (PassBuffers): a table per block, the
 // colours and the triangle work counter.
@@ -363,10 +369,15 @@ void cc_destroy(cc_ctx *ctx) {
   dev_free(c, c.scratch, c.scratch_bytes);
   dev_free(c, c.hv_scratch, c.hv_scratch_bytes);
   batch_cache_clear(c);
-  if (c.own_stream) cudaStreamDestroy(c.own_stream);
   dev_free(c, c.lut_rank, 4096 * 2);
   dev_free(c, c.lut_unrank, 13 * kUnrankStride * 2);
   dev_free(c, c.d_status, 64);
+  // the stream goes last: the frees above are ordered on it
+  cudaStreamSynchronize(c.stream);
+  if (c.own_stream) {
+    if (c.own_stream != c.stream) cudaStreamSynchronize(c.own_stream);
+    cudaStreamDestroy(c.own_stream);
+  }
   delete ctx;
 }
 

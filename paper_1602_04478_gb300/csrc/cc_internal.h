@@ -49,6 +49,7 @@ int64_t count_automorphisms(int k, const std::vector<std::pair<int, int>> &edges
 
 // ------------------------------- data graph -------------------------------
 struct DevGraph {
+  bool owned = true;          // false: device arrays belong to another context (shared graph)
   int64_t n = 0, nnz = 0, max_deg = 0;
   int64_t *row = nullptr;     // [n+1]  relabelled CSR (vertex = degree rank)
   int32_t *col = nullptr;     // [nnz]  neighbour ranks, each row ascending

@@ -112,6 +112,7 @@ struct PassBuffers {
   int *counter = nullptr;
 };
 int alloc_pass(Ctx &c, const DevGraph &g, const Plan &p, PassBuffers &B);
+size_t request_table_bytes(const Plan &p, const DevGraph &g);
 void free_pass(Ctx &c, const DevGraph &g, PassBuffers &B);
 int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers &B, u64 *status, u64 *d_per_vertex,
                  bool count_units, double *host_units);

@@ -107,13 +107,18 @@ __global__ void k_permute_colors(int64_t n, const int32_t *id_of, const uint8_t 
 static inline unsigned blocks_for(int64_t items, int per) { return (unsigned)((items + per - 1) / per); }
 
 void graph_free(Ctx &c, DevGraph &g) {
+  if (g.colors) dev_free(c, g.colors, (size_t)g.colors_T * g.n);
+  g.colors = nullptr;
+  if (!g.owned) {  // a shared graph: its arrays belong to the context that loaded it
+    g = DevGraph();
+    return;
+  }
   dev_free(c, g.row, (g.n + 1) * sizeof(int64_t));
   dev_free(c, g.col, std::max<int64_t>(g.nnz, 1) * sizeof(int32_t));
   dev_free(c, g.rev, std::max<int64_t>(g.nnz, 1) * sizeof(int64_t));
   dev_free(c, g.lo_cnt, g.n * sizeof(int32_t));
   dev_free(c, g.id_of, g.n * sizeof(int32_t));
   dev_free(c, g.rank_of, g.n * sizeof(int32_t));
-  if (g.colors) dev_free(c, g.colors, (size_t)g.colors_T * g.n);
   g = DevGraph();
 }
 
