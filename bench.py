@@ -42,6 +42,22 @@ COLOR_SEED = 1
 FLUSH_BYTES = 256 << 20
 
 
+def rank_trials(rank: int, count: int, offset: int = 0):
+    """Colourings a rank counts: ranks never share one (colourings are
+    independent, so the ranks need no data exchange)."""
+    return [rank * 1_000_000 + offset + i for i in range(count)]
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """The slowest rank's time (the job's time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_name():
     w = WORKLOAD
     return (f"chung_lu n={w['n']} mean_deg={w['mean_deg']} gamma={w['gamma']} seed={w['seed']}; "
@@ -177,6 +193,80 @@ def run_reference(args):
 
 
 # ------------------------------------ GPU arm ------------------------------------
+def run_serve(args):
+    """Serving workload: Chung-Lu graphs n in {1e4, 1e5, 1e6}, mean degree
+    8-16, exponent 2.1-2.5 resident on the device; a Poisson stream of
+    requests for treewidth-2 queries with k = 4..8 and 1-32 colourings each,
+    served by the library's continuous-batching loop (cc_server_*).  Arrival
+    rate: the given fraction of the capacity measured by a closed-loop
+    burst.  Reports p50/p99 arrival-to-result latency and throughput."""
+    import numpy as np
+
+    import graphgen as gg
+    import paper_1602_04478_gb300 as P
+
+    rng = np.random.default_rng(5)
+    sizes = [10_000, 100_000, 1_000_000]
+    graphs = []
+    for n in sizes:
+        for d in (8, 12, 16):
+            for gm in (2.1, 2.3, 2.5):
+                if n == 1_000_000 and (d, gm) != (16, 2.5) and args.serve_small:
+                    continue
+                graphs.append(gg.chung_lu(n, d, gm, int(rng.integers(1 << 30))))
+    srv = P.Server(0, workers=args.workers, memory_budget=args.serve_budget << 30)
+    gids = [srv.load_graph(g) for g in graphs]
+    qnames = ["C4", "diamond", "C5", "chord_pendant", "C6", "glasses", "C6_2pendants"]
+    qids = [srv.set_query(*gg.query(q)) for q in qnames]
+    srv.set_seed(COLOR_SEED)
+
+    big = {gid for gid, g in zip(gids, graphs) if g.n >= 1_000_000}
+
+    def make_req():
+        gid = gids[int(rng.integers(len(gids)))]
+        # the doubly annotated 8-node query runs on the generic closure path,
+        # minutes per colouring at n = 1e6: it is served on the smaller graphs
+        pool = qids[:-1] if gid in big else qids
+        return (gid, pool[int(rng.integers(len(pool)))], int(rng.integers(0, 1000)), int(rng.integers(1, 33)))
+
+    def drain(expected, submit_times):
+        got, lat = 0, []
+        while got < expected:
+            for r in srv.poll(timeout_ms=500):
+                got += 1
+                lat.append(r["done_s"] - r["submit_s"])
+        return lat
+
+    # capacity: closed-loop burst of requests
+    burst = [make_req() for _ in range(args.serve_requests // 4 or 1)]
+    t0 = time.perf_counter()
+    for rq in burst:
+        srv.submit(*rq)
+    drain(len(burst), None)
+    cap = len(burst) / (time.perf_counter() - t0)
+    out = {"impl": "ours", "mode": "serve", "graphs": len(graphs), "queries": qnames,
+           "capacity_req_per_s": cap, "requests_per_rate": args.serve_requests, "rates": []}
+    for frac in (0.7, 1.0):
+        lam = frac * cap
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=args.serve_requests))
+        reqs = [make_req() for _ in range(args.serve_requests)]
+        t0 = time.perf_counter()
+        for at, rq in zip(arrivals, reqs):
+            dt = at - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            srv.submit(*rq)
+        lat = drain(len(reqs), None)
+        wall = time.perf_counter() - t0
+        colourings = sum(r[3] for r in reqs)
+        out["rates"].append({"load": frac, "lambda_req_per_s": lam, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                             "p99_ms": 1e3 * float(np.percentile(lat, 99)), "req_per_s": len(reqs) / wall,
+                             "colorings_per_s": colourings / wall})
+    srv.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,9 +274,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-small", action="store_true", help="one n = 1e6 graph instead of nine")
+    ap.add_argument("--serve-budget", type=int, default=64, help="server table budget in GiB")
+    ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--heavy-degree", type=int, default=-1,
+                    help="heavy/light source degree threshold (default: autotuned)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
 
     import numpy as np
     import torch
@@ -215,12 +314,18 @@ def main():
     P.cc_set_coloring_seed(ctx.h, COLOR_SEED)
     units = {name: P.cc_work_units(ctx.h, gid, q) for name, q in qids.items()}
     units_step = sum(units.values())
+    if args.heavy_degree >= 0:
+        P.cc_set_heavy_degree(ctx.h, args.heavy_degree)
+        tuned = {name: args.heavy_degree for name in qids}
+    else:
+        tuned = {name: P.cc_autotune(ctx.h, gid, q) for name, q in qids.items()}
     trial_base = rank * 1_000_000
 
     def step(i):
         out = {}
+        trial = rank_trials(rank, 1, i)[0]
         for name, q in qids.items():
-            col, _, _ = ctx.count(gid, q, trial_base + i, 1)
+            col, _, _ = ctx.count(gid, q, trial, 1)
             out[name] = int(col[0])
         return out
 
@@ -250,25 +355,42 @@ def main():
     ms = sum(a.elapsed_time(b) for a, b in evs)
     kern = P.cc_get_timing(ctx.h)
     P.cc_set_timing(ctx.h, False)
-    if dist is not None:
-        t = torch.tensor([ms], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, device=f"cuda:{local}")
     value = units_step * args.steps * world / (ms / 1e3) / 1e9
     colourings = len(qids) * args.steps * world / (ms / 1e3)
     launches = sum(c for _, c in kern.values())
 
-    # dominant kernel and its roofline (algorithmic bytes: 8 bytes per
-    # edge-subset update, one u64 table entry read per update)
-    dom = max(kern.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_n) = dom
-    dom_units = units["C6"] if dom_name == "cycle_closure" else units["glasses"]
-    dom_units_per_launch = dom_units * args.steps / max(1, dom_n)
+    # Roofline of the dominant stage: the C6 root-cycle closure, a sequence of
+    # kernels per colouring (heavy-source level builds and pulls, the per-CTA
+    # push for the other sources).  Algorithmic bytes: 8 bytes per
+    # edge-subset update (one u64 table entry read per update).
+    closure = [k for k in kern if k.startswith("cycle_")]
+    clo_ms = sum(kern[k][0] for k in closure)
+    per_colouring_ms = clo_ms / args.steps
     peak, peak_kind = measured_peaks()
-    achieved = 8.0 * dom_units_per_launch / (dom_ms / dom_n / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
-                "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "avg_launch_ms": dom_ms / dom_n, "share_of_step": dom_ms / ms}
+    achieved = 8.0 * units["C6"] / (per_colouring_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "C6 root-cycle closure (" + " + ".join(sorted(closure)) + ")",
+                "achieved": achieved, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "avg_launch_ms": per_colouring_ms,
+                "launches_per_colouring": sum(kern[k][1] for k in closure) / args.steps,
+                "share_of_step": clo_ms / ms}
+
+    # batched form: the same kind of step (one colouring of each query per
+    # step) for K colourings in one cc_count_batch call, recorded once as a
+    # CUDA graph and then replayed; timed on the host around the synchronous call
+    reqs = [(gid, q, trial_base + 20_000, args.steps) for q in qids.values()]
+    P.cc_count_batch(ctx.h, reqs)  # eager run + capture (untimed)
+    barrier()
+    tb0 = time.perf_counter()
+    reps = 2
+    for _ in range(reps):
+        P.cc_count_batch(ctx.h, reqs)
+    barrier()
+    batched_s = (time.perf_counter() - tb0) / reps
+    batched = {"value": units_step * args.steps * world / batched_s / 1e9, "unit": UNIT,
+               "colorings_per_s": len(qids) * args.steps * world / batched_s,
+               "ms_per_step": 1e3 * batched_s / args.steps, "timing": "host clock around synchronous calls",
+               "form": f"{len(qids)} requests x {args.steps} colourings per cc_count_batch call, CUDA-graph replay"}
 
     # end to end through the C-ABI with host buffers: load the CSR from host
     # memory, count both queries, read the counts back, free the graph
@@ -292,7 +414,7 @@ def main():
             "config": {"workload": workload_name(), **WORKLOAD, "parallelism": f"replicas x{world}",
                        "l2": "256 MB flush between steps, outside the events; working set > L2",
                        "units_per_step": units_step, "units_by_query": units},
-            "colorings_per_s": colourings, "wall_s": wall,
+            "colorings_per_s": colourings, "wall_s": wall, "batched": batched, "heavy_degree": tuned,
             "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kern.items()},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "e2e": e2e,
             "counts_first_step": counts[0] if counts else None}

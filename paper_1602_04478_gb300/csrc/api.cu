@@ -264,15 +264,29 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
         a.Ebw[j] = tab_e(T, st.edge_child[j], st.edge_fwd[j]);
         plain = plain && st.node_child[j] < 0 && st.edge_child[j] < 0;
       }
-      if (plain) {
-        a.n_h = 1;
-        a.hs[0] = 0;
-        a.multiplier = st.L;
-      } else {
-        a.n_h = st.L;
-        for (int h = 0; h < st.L; h++) a.hs[h] = h;
-        a.multiplier = 1;
+      // Rotations of the cycle that carry every annotation onto an identical
+      // child subtree map the matches with a_h highest onto those with
+      // a_{h+rho} highest: compute h < rho and multiply by L / rho.
+      int rho = st.L;
+      for (int r = 1; r < st.L; r++) {
+        if (st.L % r) continue;
+        bool ok = true;
+        for (int j = 0; j < st.L && ok; j++) {
+          int t = (j + r) % st.L;
+          auto sig_of = [&](int child) { return child < 0 ? std::string("-") : p.stages[child].sig; };
+          ok = sig_of(st.node_child[j]) == sig_of(st.node_child[t]) &&
+               sig_of(st.edge_child[j]) == sig_of(st.edge_child[t]) &&
+               (st.edge_child[j] < 0 || st.edge_fwd[j] == st.edge_fwd[t]);
+        }
+        if (ok) {
+          rho = r;
+          break;
+        }
       }
+      (void)plain;
+      a.n_h = rho;
+      for (int h = 0; h < rho; h++) a.hs[h] = h;
+      a.multiplier = st.L / rho;
       a.per_vertex = d_per_vertex;
       a.status = status;
       a.count_units = count_units;

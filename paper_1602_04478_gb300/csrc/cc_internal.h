@@ -29,6 +29,7 @@ struct Stage {
   bool edge_fwd[kMaxK];      // child's first boundary node is nodes[i]
   int s = 0;                 // |SQ(B)|: query nodes of the represented subquery
   uint32_t sq_mask = 0;
+  std::string sig;           // structure of the block's subtree: equal strings, equal tables
 };
 
 struct Plan {

@@ -285,7 +285,31 @@ int validate(int k, const std::vector<std::pair<int, int>> &edges) {
   return CC_OK;
 }
 
+// Structural signature of each block: kind, size, boundary count and the
+// annotating children by position (cycle positions relative to the block's
+// own node order).  Two blocks with equal signatures represent isomorphic
+// subqueries with the same boundary roles, so their tables are equal.
+void signatures(Plan &p) {
+  for (auto &st : p.stages) {
+    std::string g = std::to_string(st.kind) + "/" + std::to_string(st.L) + "/" + std::to_string(st.s) + "/" +
+                    std::to_string(st.nb) + "[";
+    int ne = st.kind == ST_LEAF ? 1 : (st.kind == ST_ROOT_NODE ? 0 : st.L);
+    for (int i = 0; i < st.L; i++) {
+      bool bdn = st.nb > 0 && (st.nodes[i] == st.bd[0] || (st.nb > 1 && st.nodes[i] == st.bd[1]));
+      g += (bdn ? "b" : "n");
+      g += st.node_child[i] >= 0 ? "(" + p.stages[st.node_child[i]].sig + ")" : "-";
+      if (i < ne) {
+        g += st.edge_child[i] >= 0 ? std::string(st.edge_fwd[i] ? "F" : "R") + "(" + p.stages[st.edge_child[i]].sig + ")"
+                                   : "e";
+      }
+      g += ",";
+    }
+    st.sig = g + "]";
+  }
+}
+
 void finish(Plan &p, int k, const std::vector<std::pair<int, int>> &edges) {
+  signatures(p);
   p.k = k;
   p.edges = edges;
   p.aut = count_automorphisms(k, edges);

@@ -361,3 +361,18 @@ def test_autotune_keeps_counts(cc):
         assert [int(x) for x in res[0]] == before
     finally:
         cc.free_graph(gid)
+
+
+@pytest.mark.parametrize("gname", ["er2000", "cl3000", "rmat10"])
+@pytest.mark.parametrize("L", [4, 5, 6])
+def test_work_units_match_oracle(cc, gname, L):
+    # the benchmark's work unit, counted on the device, equals the oracle's
+    # plain-loop structural count of the DB procedure
+    import paper_1602_04478_gb300 as P
+    g = graph(gname)
+    gid = cc.load_graph(g)
+    try:
+        qid = cc.set_query(*gg.cycle(L))
+        assert P.cc_work_units(cc.h, gid, qid) == O.cycle_units(g, L, L)
+    finally:
+        cc.free_graph(gid)
