@@ -267,6 +267,24 @@ def run_serve(args):
     return 0
 
 
+def run_profile_case(args):
+    """One colouring of one query on the benchmark graph, nothing else: the
+    command a profiler wraps to capture a few launches of one kernel."""
+    import graphgen as gg
+    import paper_1602_04478_gb300 as P
+
+    g = make_graph()
+    ctx = P.Context(0)
+    gid = ctx.load_graph(g)
+    P.cc_set_coloring_seed(ctx.h, COLOR_SEED)
+    P.cc_set_heavy_degree(ctx.h, args.heavy_degree if args.heavy_degree >= 0 else 256)
+    q = ctx.set_query(*gg.query(args.profile_case))
+    col, _, _ = ctx.count(gid, q, 0, 1)
+    print(json.dumps({"profile_case": args.profile_case, "colorful": int(col[0]),
+                      "kernel_launches": P.cc_kernel_launches(ctx.h)}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -281,7 +299,11 @@ def main():
     ap.add_argument("--workers", type=int, default=4)
     ap.add_argument("--heavy-degree", type=int, default=-1,
                     help="heavy/light source degree threshold (default: autotuned)")
+    ap.add_argument("--profile-case", default=None, metavar="QUERY",
+                    help="count QUERY once on the benchmark graph (one colouring, no timing) for profiler captures")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:
@@ -338,6 +360,7 @@ def main():
     sampler = ClockSampler(local)
     barrier()
     sampler.start()
+    launches0 = P.cc_kernel_launches(ctx.h)
     evs = []
     counts = []
     wall0 = time.perf_counter()
@@ -351,6 +374,7 @@ def main():
         evs.append((a, b))
     barrier()
     wall = time.perf_counter() - wall0
+    launches = P.cc_kernel_launches(ctx.h) - launches0
     clocks = sampler.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs)
     kern = P.cc_get_timing(ctx.h)
@@ -358,7 +382,6 @@ def main():
     ms = max_over_ranks(ms, dist, device=f"cuda:{local}")
     value = units_step * args.steps * world / (ms / 1e3) / 1e9
     colourings = len(qids) * args.steps * world / (ms / 1e3)
-    launches = sum(c for _, c in kern.values())
 
     # Roofline of the dominant stage: the C6 root-cycle closure, a sequence of
     # kernels per colouring (heavy-source level builds and pulls, the per-CTA

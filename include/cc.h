@@ -227,6 +227,12 @@ int cc_set_timing(cc_ctx *ctx, int enable);
 int cc_get_timing(cc_ctx *ctx, char *names, double *ms, int64_t *launches, int cap);
 int cc_reset_timing(cc_ctx *ctx);
 
+/* Kernels this context has launched since it was created, counting the
+ * library's own kernels only (not memsets, copies or the sorting library's
+ * kernels used while loading a graph); a replayed batch graph adds the
+ * kernels it holds.  Counting needs no timing and no synchronisation. */
+int cc_kernel_launches(cc_ctx *ctx, uint64_t *launches);
+
 /* Count without any device allocation by the library (the paper has no
  * counterpart; it is for callers that cannot let a library allocate GPU
  * memory, e.g. code that owns a fixed device arena or runs where cudaMalloc

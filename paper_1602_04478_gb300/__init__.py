@@ -33,7 +33,7 @@ EXPORTED = [
     "cc_load_csr", "cc_free_graph",
     "cc_graph_info", "cc_set_query", "cc_set_decomposition", "cc_plan_inspect", "cc_query_info", "cc_set_coloring_seed",
     "cc_set_colors", "cc_clear_colors", "cc_count", "cc_count_per_vertex", "cc_work_units", "cc_set_timing",
-    "cc_get_timing", "cc_reset_timing", "cc_count_cycle_noalloc", "cc_count_batch", "cc_set_graph_capture",
+    "cc_get_timing", "cc_reset_timing", "cc_kernel_launches", "cc_count_cycle_noalloc", "cc_count_batch", "cc_set_graph_capture",
     "cc_autotune", "cc_server_create", "cc_server_destroy", "cc_server_load_csr", "cc_server_set_query",
     "cc_server_set_coloring_seed", "cc_server_submit", "cc_server_poll", "cc_server_stats", "cc_strerror",
 ]
@@ -100,6 +100,7 @@ def lib():
             "cc_set_timing": ([P, ctypes.c_int], ctypes.c_int),
             "cc_get_timing": ([P, ctypes.c_char_p, DP, I64P, ctypes.c_int], ctypes.c_int),
             "cc_reset_timing": ([P], ctypes.c_int),
+            "cc_kernel_launches": ([P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
             "cc_count_cycle_noalloc": ([ctypes.c_int, P, ctypes.c_int, I64, P, P, P, U64P], ctypes.c_int),
             "cc_count_batch": ([P, ctypes.POINTER(cc_request), ctypes.c_int, U64P, ctypes.POINTER(ctypes.c_int)],
                                ctypes.c_int),
@@ -296,6 +297,12 @@ def cc_get_timing(h, cap: int = 64):
         nm = names.raw[48 * i:48 * (i + 1)].split(b"\0", 1)[0].decode()
         out[nm] = (float(ms[i]), int(cnt[i]))
     return out
+
+
+def cc_kernel_launches(h) -> int:
+    out = ctypes.c_uint64(0)
+    _check(lib().cc_kernel_launches(h, ctypes.byref(out)), "cc_kernel_launches")
+    return int(out.value)
 
 
 def cc_reset_timing(h) -> None:

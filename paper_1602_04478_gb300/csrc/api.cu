@@ -684,6 +684,12 @@ int cc_get_timing(cc_ctx *ctx, char *names, double *ms, int64_t *launches, int c
   return (int)ctx->c.times.size();
 }
 
+int cc_kernel_launches(cc_ctx *ctx, uint64_t *launches) {
+  if (!ctx || !launches) return CC_ERR_INVALID_ARG;
+  *launches = ctx->c.kernels;
+  return CC_OK;
+}
+
 int cc_reset_timing(cc_ctx *ctx) {
   if (!ctx) return CC_ERR_INVALID_ARG;
   timing_flush(ctx->c);

@@ -25,6 +25,7 @@ struct Ctx::BatchCache {
   u64 *results = nullptr;         // [total trials][8] status words
   size_t total = 0;
   cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;           // kernels one replay launches
 };
 
 void batch_cache_clear(Ctx &c) {
@@ -109,6 +110,7 @@ extern "C" int cc_count_batch(cc_ctx *ctx, const cc_request *reqs, int n_reqs, u
     b = it->second;
     timing_begin(c, "batch_graph");
     rc = cudaGraphLaunch(b->exec, c.stream) == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+    if (rc == CC_OK) c.kernels += b->kernels;
     timing_end(c);
   } else {
     // a stale entry, or too many distinct batches held: start the cache afresh
@@ -130,7 +132,10 @@ extern "C" int cc_count_batch(cc_ctx *ctx, const cc_request *reqs, int n_reqs, u
       c.timing = false;
       cudaGraph_t graph = nullptr;
       if (rc == CC_OK && cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const uint64_t k0 = c.kernels;
         int rc2 = enqueue_batch(c, reqs, n_reqs, *b);
+        b->kernels = c.kernels - k0;  // recorded, not launched
+        c.kernels = k0;
         cudaError_t e = cudaStreamEndCapture(c.stream, &graph);
         if (rc2 == CC_OK && e == cudaSuccess && graph &&
             cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess) {

@@ -97,6 +97,7 @@ struct Ctx {
   bool capture = true;           // batches replay a captured CUDA graph
   struct BatchCache;
   std::map<std::string, BatchCache *> batches;
+  uint64_t kernels = 0;          // kernels launched by this context (a graph replay adds those it holds)
   // timing
   bool timing = false;
   std::map<std::string, std::pair<double, int64_t>> times;

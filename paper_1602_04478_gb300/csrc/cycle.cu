@@ -603,6 +603,7 @@ int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   timing_begin(c, "cycle_closure");
   k_cycle<<<slots, kCtaThreads, smem, c.stream>>>(a, sc, counter);
+  c.kernels++;
   timing_end(c);
   // the queue counter returns to zero too: the whole scratch is zero between launches
   if (cudaMemsetAsync(counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;

@@ -603,20 +603,33 @@ int run_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank, int B) {
               G.B);
       timing_begin(c, "cycle_heavy_levels");
       k_hv_level1<<<g1, 256, 0, c.stream>>>(a, S, G, h);
+      c.kernels++;
       for (int hf = 0; hf < 2; hf++)
-        if (S.mat[hf] >= 1) k_hv_join<<<sms * 4, 256, 0, c.stream>>>(a, S, G, h, hf, 1);
+        if (S.mat[hf] >= 1) {
+          k_hv_join<<<sms * 4, 256, 0, c.stream>>>(a, S, G, h, hf, 1);
+          c.kernels++;
+        }
       for (int j = 1; j < std::max(S.mat[0], S.mat[1]); j++) {
         for (int hf = 0; hf < 2; hf++)
-          if (S.mat[hf] >= j + 1) k_hv_push<<<sms * 8, 256, 0, c.stream>>>(a, S, G, h, hf, j);
+          if (S.mat[hf] >= j + 1) {
+            k_hv_push<<<sms * 8, 256, 0, c.stream>>>(a, S, G, h, hf, j);
+            c.kernels++;
+          }
         for (int hf = 0; hf < 2; hf++)
-          if (S.mat[hf] >= j + 1) k_hv_join<<<sms * 4, 256, 0, c.stream>>>(a, S, G, h, hf, j + 1);
+          if (S.mat[hf] >= j + 1) {
+            k_hv_join<<<sms * 4, 256, 0, c.stream>>>(a, S, G, h, hf, j + 1);
+            c.kernels++;
+          }
       }
       timing_end(c);
       timing_begin(c, "cycle_heavy_pull");
       k_hv_pull<<<sms * 4, kHvThreads, smem, c.stream>>>(a, S, G, h, x_split);
+      c.kernels++;
       timing_end(c);
       k_hv_clear<<<sms * 2, 256, 0, c.stream>>>(a, S, G);
+      c.kernels++;
       k_hv_finish<<<1, 32, 0, c.stream>>>(a, S, G, hi == a.n_h - 1);
+      c.kernels++;
     }
   }
   // leave the level counts at zero as well: the scratch is all zero between launches

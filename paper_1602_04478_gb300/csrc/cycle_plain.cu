@@ -477,6 +477,7 @@ int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank) {
   else
     k_pc_light<6><<<slots, kPlThreads, 0, c.stream>>>(a.g, a.colors, S, end_rank, work, a.multiplier,
                                                        a.per_vertex, a.status, a.k);
+  c.kernels++;
   timing_end(c);
   // the queue counter returns to zero too: the whole scratch is zero between launches
   if (cudaMemsetAsync(work, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
@@ -497,12 +498,16 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, int32_t x
             G.B);
     timing_begin(c, "cycle_plain_levels");
     k_pc_levels<L><<<gl, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G);
+    c.kernels++;
     timing_end(c);
     timing_begin(c, "cycle_plain_pull");
     k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G, x_split, a.k);
+    c.kernels++;
     timing_end(c);
     k_pc_clear<L><<<sms, 256, 0, c.stream>>>(a.g, a.colors, S, G);
+    c.kernels++;
     k_pc_finish<<<1, 32, 0, c.stream>>>(S, G, a.multiplier, a.per_vertex, a.status);
+    c.kernels++;
   }
   return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }

@@ -173,9 +173,11 @@ int graph_load(Ctx &c, int64_t n, const int64_t *row_ptr, const int32_t *col, in
       break;
     }
     k_degree_keys<<<blocks_for(n, 256), 256, 0, st>>>(n, d_rp, k0);
+    c.kernels++;
     size_t tbx = tb;
     if (cub::DeviceRadixSort::SortKeys(tmp, tbx, k0, k1, n, 0, 64, st) != cudaSuccess) { rc = CC_ERR_CUDA; break; }
     k_rank_of<<<blocks_for(n, 256), 256, 0, st>>>(n, k1, g.id_of, g.rank_of);
+    c.kernels++;
     // rank-ordered row pointers on the host (degrees are known there)
     std::vector<int32_t> id_of(n);
     if (cudaMemcpyAsync(id_of.data(), g.id_of, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -192,11 +194,14 @@ int graph_load(Ctx &c, int64_t n, const int64_t *row_ptr, const int32_t *col, in
     }
     if (nnz > 0) {
       k_edge_keys<<<blocks_for(n * 32, 256), 256, 0, st>>>(n, d_rp, d_col, g.rank_of, k0, c.d_status);
+      c.kernels++;
       tbx = tb;
       if (cub::DeviceRadixSort::SortKeys(tmp, tbx, k0, k1, nnz, 0, 64, st) != cudaSuccess) { rc = CC_ERR_CUDA; break; }
       k_split_keys<<<blocks_for(nnz, 256), 256, 0, st>>>(nnz, k1, g.col);
+      c.kernels++;
     }
     k_finish_rows<<<blocks_for(n * 32, 256), 256, 0, st>>>(n, g.row, g.col, g.rev, g.lo_cnt, c.d_status);
+    c.kernels++;
     unsigned long long status[4];
     if (cudaMemcpyAsync(status, c.d_status, sizeof(status), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
@@ -217,6 +222,7 @@ int colors_fill(Ctx &c, const DevGraph &g, int k, int64_t trial, uint8_t *d_out)
     cudaMemcpyAsync(d_out, g.colors + (size_t)trial * g.n, g.n, cudaMemcpyDeviceToDevice, c.stream);
   } else {
     k_colors<<<blocks_for(g.n, 256), 256, 0, c.stream>>>(g.n, g.id_of, c.seed, trial, k, d_out);
+    c.kernels++;
   }
   return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }
@@ -236,6 +242,7 @@ int colors_set(Ctx &c, DevGraph &g, const uint8_t *h_colors, int T) {
   for (int t = 0; t < T; t++) {
     CK(cudaMemcpyAsync(d_by_id, h_colors + (size_t)t * g.n, g.n, cudaMemcpyHostToDevice, c.stream));
     k_permute_colors<<<blocks_for(g.n, 256), 256, 0, c.stream>>>(g.n, g.id_of, d_by_id, d + (size_t)t * g.n);
+    c.kernels++;
   }
   CK(cudaStreamSynchronize(c.stream));
   dev_free(c, d_by_id, g.n);

@@ -104,6 +104,7 @@ int launch_leaf(Ctx &c, const LeafArgs &a) {
   if (blocks < 1) blocks = 1;
   timing_begin(c, "leaf_join");
   k_leaf_join<<<(unsigned)blocks, 256, smem, c.stream>>>(a);
+  c.kernels++;
   timing_end(c);
   return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }
@@ -127,6 +128,7 @@ int launch_root_sum(Ctx &c, const GraphView &g, const u64 *table, u64 *per_verte
   if (blocks < 1) blocks = 1;
   timing_begin(c, "root_sum");
   k_root_sum<<<(unsigned)blocks, 256, 0, c.stream>>>(g.n, table, per_vertex, status);
+  c.kernels++;
   timing_end(c);
   return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }

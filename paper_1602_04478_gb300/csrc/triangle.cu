@@ -15,27 +15,58 @@
 // row of the boundary image(s) (unary row, or the directed-edge row of the
 // boundary pair, which is a data edge because triangle nodes are pairwise
 // adjacent), or to the root count.
-// One warp per source u, sources taken highest first from a work counter.
+//
+// Two kernels share the per-triangle work:
+//  * k_triangle_hub, one CTA per source u of degree >= kHubDegree: the CTA
+//    puts N<(u) into a shared-memory hash set (open addressing, at most half
+//    full), then its warps scan the wedges (v, w) and test w against the set
+//    in O(1); contributions to u's own output row gather in shared memory and
+//    reach the table once per source.  On skewed graphs these sources hold
+//    almost all wedges.
+//  * k_triangle, one warp per remaining source, w tested by binary search in
+//    the sorted N<(u).
+// A wedge whose first two vertices share a colour cannot close a colourful
+// triangle, so v with chi(v) = chi(u) is skipped before its list is read.
+#include <algorithm>
+
 #include "cc_kernels.h"
 
 namespace cc {
 
 constexpr int kMaxPartial = 128;
+constexpr int kHubDegree = 32;        // sources of at least this degree take the CTA kernel
+constexpr int kHubMaxSlots = 16384;   // hash slots per CTA (N<(u) of up to 8192 vertices)
+constexpr int kHubThreads = 256;
 
 struct TriEdges {
   int64_t pos[3][3];  // pos[i][j]: CSR position of directed edge p_i -> p_j (local ids 0=u,1=v,2=w)
 };
 
-__device__ void tri_emit_plain(const TriArgs &a, const int32_t vx[3], const int c[3], const TriEdges &te,
-                               u64 &root_acc, unsigned &ovf) {
+// Where unary contributions go: the output table, except those to vertex u
+// when the caller gathers u's row in shared memory (acc != nullptr).
+struct USink {
+  int32_t u = -1;
+  u64 *acc = nullptr;
+};
+
+__device__ __forceinline__ void emit_unary(const TriArgs &a, const USink &sk, int32_t x, int slot, u64 v,
+                                           unsigned &ovf) {
+  if (x == sk.u) atomic_add_ck(sk.acc + slot, v, ovf);
+  else atomic_add_ck(a.out + (int64_t)x * a.R_out + slot, v, ovf);
+}
+
+__device__ void tri_emit_plain(const TriArgs &a, const USink &sk, const int32_t vx[3], const int c[3],
+                               const TriEdges &te, u64 &root_acc, unsigned &ovf) {
   uint32_t S = (1u << c[0]) | (1u << c[1]) | (1u << c[2]);
   if (a.nb == 0) {
     root_acc = add_ck(root_acc, 6ull, ovf);
   } else if (a.nb == 1) {
-    for (int i = 0; i < 3; i++)
-      atomic_add_ck(a.out + (int64_t)vx[i] * a.R_out + uslot(a.lut, S, c[i]), 2ull, ovf);
+#pragma unroll
+    for (int i = 0; i < 3; i++) emit_unary(a, sk, vx[i], uslot(a.lut, S, c[i]), 2ull, ovf);
   } else {
+#pragma unroll
     for (int i = 0; i < 3; i++)
+#pragma unroll
       for (int j = 0; j < 3; j++)
         if (i != j) atomic_add_ck(a.out + te.pos[i][j] * a.R_out + pslot(a.lut, S, c[i], c[j]), 1ull, ovf);
   }
@@ -71,8 +102,8 @@ __device__ int tri_join(uint16_t *pm, u64 *pv, int np, const u64 *row, int R, in
   return nn;
 }
 
-__device__ void tri_emit_general(const TriArgs &a, const int32_t vx[3], const int c[3], const TriEdges &te,
-                                 u64 &root_acc, unsigned &ovf) {
+__device__ void tri_emit_general(const TriArgs &a, const USink &sk, const int32_t vx[3], const int c[3],
+                                 const TriEdges &te, u64 &root_acc, unsigned &ovf) {
   // all six assignments (a0, a1, a2) -> local vertices (perm[0], perm[1], perm[2])
   const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
   for (int pi = 0; pi < 6; pi++) {
@@ -103,7 +134,7 @@ __device__ void tri_emit_general(const TriArgs &a, const int32_t vx[3], const in
         root_acc = add_ck(root_acc, pv[q], ovf);
       } else if (a.nb == 1) {
         int lb = p[a.bd[0]];
-        atomic_add_ck(a.out + (int64_t)vx[lb] * a.R_out + uslot(a.lut, pm[q], c[lb]), pv[q], ovf);
+        emit_unary(a, sk, vx[lb], uslot(a.lut, pm[q], c[lb]), pv[q], ovf);
       } else {
         int l0 = p[a.bd[0]], l1 = p[a.bd[1]];
         atomic_add_ck(a.out + te.pos[l0][l1] * a.R_out + pslot(a.lut, pm[q], c[l0], c[l1]), pv[q], ovf);
@@ -112,67 +143,127 @@ __device__ void tri_emit_general(const TriArgs &a, const int32_t vx[3], const in
   }
 }
 
+// x[i] for a runtime i in 0..2 without indexing a local array
+template <class T>
+__device__ __forceinline__ T pick3(const T x[3], int i) {
+  return i == 0 ? x[0] : (i == 1 ? x[1] : x[2]);
+}
+// te.pos[i][j] for runtime i != j
+__device__ __forceinline__ int64_t tpos(const TriEdges &te, int i, int j) {
+  return i == 0 ? (j == 1 ? te.pos[0][1] : te.pos[0][2])
+                : (i == 1 ? (j == 0 ? te.pos[1][0] : te.pos[1][2]) : (j == 0 ? te.pos[2][0] : te.pos[2][1]));
+}
+
 // One annotation only (a node table at position ai, or an edge table on edge
 // ai -> ai+1): each of its row's signatures extends the triangle's colours
 // directly, without partial lists.
-__device__ __forceinline__ void tri_emit_one(const TriArgs &a, const int32_t vx[3], const int c[3],
+__device__ __forceinline__ void tri_emit_one(const TriArgs &a, const USink &sk, const int32_t vx[3], const int c[3],
                                              const TriEdges &te, u64 &root_acc, unsigned &ovf, int ai, bool edge) {
-  const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
   const uint32_t K = (1u << a.k) - 1u;
+  const uint32_t base = (1u << c[0]) | (1u << c[1]) | (1u << c[2]);
+  if (a.nb == 0 && !edge) {
+    // root, one node table: the signature is the full colour set, so the
+    // value of an assignment depends only on which vertex takes a_ai, and
+    // each vertex takes it in two of the six assignments
+    const TabU &N = a.N[ai];
+    u64 t = 0;
+#pragma unroll
+    for (int x = 0; x < 3; x++)
+      t = add_ck(t, __ldg(N.p + (int64_t)vx[x] * N.R + uslot(a.lut, (K & ~base) | (1u << c[x]), c[x])), ovf);
+    root_acc = add_ck(root_acc, add_ck(t, t, ovf), ovf);
+    return;
+  }
+  const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+#pragma unroll
   for (int pi = 0; pi < 6; pi++) {
     const int *p = perms[pi];
-    const uint32_t base = (1u << c[p[0]]) | (1u << c[p[1]]) | (1u << c[p[2]]);
-    const int li = p[ai], lj = p[(ai + 1) % 3];
+    const int li = pick3(p, ai), lj = pick3(p, ai == 2 ? 0 : ai + 1);
+    const int cli = pick3(c, li), clj = pick3(c, lj);
     const u64 *row;
     int R, s;
     uint32_t shared;
     if (edge) {
       const TabE &E = a.E[ai];
-      int64_t e = E.use_rev ? te.pos[lj][li] : te.pos[li][lj];
+      int64_t e = E.use_rev ? tpos(te, lj, li) : tpos(te, li, lj);
       row = E.p + e * E.R;
       R = E.R;
       s = E.s;
-      shared = (1u << c[li]) | (1u << c[lj]);
+      shared = (1u << cli) | (1u << clj);
     } else {
       const TabU &N = a.N[ai];
-      row = N.p + (int64_t)vx[li] * N.R;
+      row = N.p + (int64_t)pick3(vx, li) * N.R;
       R = N.R;
       s = N.s;
-      shared = 1u << c[li];
+      shared = 1u << cli;
     }
     if (a.nb == 0) {
-      // the root's signature is the full colour set: one compatible slot
       uint32_t m = (K & ~base) | shared;
-      int slot = edge ? pslot(a.lut, m, c[li], c[lj]) : uslot(a.lut, m, c[li]);
+      int slot = edge ? pslot(a.lut, m, cli, clj) : uslot(a.lut, m, cli);
       root_acc = add_ck(root_acc, __ldg(row + slot), ovf);
       continue;
     }
+    const int lb = pick3(p, a.bd[0]);
+    const int lb1 = a.nb == 2 ? pick3(p, a.bd[1]) : lb;
     for (int j = 0; j < R; j++) {
       u64 t = __ldg(row + j);
       if (!t) continue;
-      uint32_t mt = edge ? pmask(a.lut, s, j, c[li], c[lj]) : umask(a.lut, s, j, c[li]);
+      uint32_t mt = edge ? pmask(a.lut, s, j, cli, clj) : umask(a.lut, s, j, cli);
       if ((mt & base) != shared) continue;
       uint32_t m = mt | base;
       if (a.nb == 1) {
-        int lb = p[a.bd[0]];
-        atomic_add_ck(a.out + (int64_t)vx[lb] * a.R_out + uslot(a.lut, m, c[lb]), t, ovf);
+        emit_unary(a, sk, pick3(vx, lb), uslot(a.lut, m, pick3(c, lb)), t, ovf);
       } else {
-        int l0 = p[a.bd[0]], l1 = p[a.bd[1]];
-        atomic_add_ck(a.out + te.pos[l0][l1] * a.R_out + pslot(a.lut, m, c[l0], c[l1]), t, ovf);
+        atomic_add_ck(a.out + tpos(te, lb, lb1) * a.R_out + pslot(a.lut, m, pick3(c, lb), pick3(c, lb1)), t, ovf);
       }
     }
   }
 }
 
-__global__ void __launch_bounds__(256) k_triangle(TriArgs a, bool plain, int one_pos, bool one_edge) {
+// How the kernels emit a listed triangle: which of the forms above, and
+// whether the directed-edge positions are needed (edge tables or an
+// edge-keyed output).
+struct TriMode {
+  bool plain = true;
+  int one_pos = -1;
+  bool one_edge = false;
+  bool need_pos = false;
+};
+
+// One colourful triangle u > v > w: u->v at CSR position p01, u->w at p02,
+// v->w at p12.  kForm: 0 plain, 1 one annotation, 2 general.
+template <int kForm>
+__device__ __forceinline__ void tri_visit(const TriArgs &a, const TriMode &md, const USink &sk, int32_t u,
+                                          int32_t v, int32_t w, int cu, int cv, int cw, int64_t p01, int64_t p02,
+                                          int64_t p12, u64 &root_acc, unsigned &ovf) {
+  int32_t vx[3] = {u, v, w};
+  int c[3] = {cu, cv, cw};
+  TriEdges te;
+  if (md.need_pos) {
+    te.pos[0][1] = p01;
+    te.pos[0][2] = p02;
+    te.pos[1][2] = p12;
+    te.pos[1][0] = __ldg(a.g.rev + p01);
+    te.pos[2][0] = __ldg(a.g.rev + p02);
+    te.pos[2][1] = __ldg(a.g.rev + p12);
+    te.pos[0][0] = te.pos[1][1] = te.pos[2][2] = -1;
+  }
+  if (kForm == 0) tri_emit_plain(a, sk, vx, c, te, root_acc, ovf);
+  else if (kForm == 1) tri_emit_one(a, sk, vx, c, te, root_acc, ovf, md.one_pos, md.one_edge);
+  else tri_emit_general(a, sk, vx, c, te, root_acc, ovf);
+}
+
+// One warp per source u in [0, u_end), highest first.
+template <int kForm>
+__global__ void __launch_bounds__(256) k_triangle(TriArgs a, TriMode md, int32_t u_end) {
   const int lane = threadIdx.x & 31;
+  USink sk;
   unsigned ovf = 0;
   while (true) {
     int idx = 0;
     if (lane == 0) idx = atomicAdd(a.work_counter, 1);
     idx = __shfl_sync(0xffffffffu, idx, 0);
-    if (idx >= a.g.n) break;
-    const int32_t u = (int32_t)(a.g.n - 1 - idx);
+    if (idx >= u_end) break;
+    const int32_t u = u_end - 1 - idx;
     const int64_t ub = a.g.row[u];
     const int du = a.g.lo_cnt[u];
     const int cu = a.colors[u];
@@ -180,31 +271,20 @@ __global__ void __launch_bounds__(256) k_triangle(TriArgs a, bool plain, int one
     u64 units = 0;
     for (int iv = 1; iv < du; iv++) {
       const int32_t v = __ldg(a.g.col + ub + iv);
-      const int cv = a.colors[v];
-      const int64_t vb = a.g.row[v];
       const int dv = a.g.lo_cnt[v];
       units += (u64)dv;
+      const int cv = a.colors[v];
+      if (cv == cu) continue;
+      const int64_t vb = a.g.row[v];
       for (int j = lane; j < dv; j += 32) {
         const int32_t w = __ldg(a.g.col + vb + j);
-        // w must be a lower neighbour of u below v: search N<(u)[0, iv)
+        // w < v is a lower neighbour of u: search N<(u)[0, iv)
         int64_t p = lower_bound_i32(a.g.col, ub, ub + iv, w);
         if (p >= ub + iv || __ldg(a.g.col + p) != w) continue;
         const int cw = a.colors[w];
         // a colourful match maps the triangle to three distinct colours
-        if (cu == cv || cu == cw || cv == cw) continue;
-        int32_t vx[3] = {u, v, w};
-        int c[3] = {cu, cv, cw};
-        TriEdges te;
-        te.pos[0][1] = ub + iv;
-        te.pos[0][2] = p;
-        te.pos[1][2] = vb + j;
-        te.pos[1][0] = __ldg(a.g.rev + te.pos[0][1]);
-        te.pos[2][0] = __ldg(a.g.rev + te.pos[0][2]);
-        te.pos[2][1] = __ldg(a.g.rev + te.pos[1][2]);
-        te.pos[0][0] = te.pos[1][1] = te.pos[2][2] = -1;
-        if (plain) tri_emit_plain(a, vx, c, te, root_acc, ovf);
-        else if (one_pos >= 0) tri_emit_one(a, vx, c, te, root_acc, ovf, one_pos, one_edge);
-        else tri_emit_general(a, vx, c, te, root_acc, ovf);
+        if (cu == cw || cv == cw) continue;
+        tri_visit<kForm>(a, md, sk, u, v, w, cu, cv, cw, ub + iv, p, vb + j, root_acc, ovf);
       }
     }
     if (a.count_units && lane == 0 && units) atomicAdd(a.status + ST_UNITS, units);
@@ -220,21 +300,180 @@ __global__ void __launch_bounds__(256) k_triangle(TriArgs a, bool plain, int one
   if (ovf & 2u) atomicOr(a.status + ST_TIMEOUT, 2ull);  // partial list capacity exceeded
 }
 
-int launch_triangle(Ctx &c, const TriArgs &a) {
-  bool plain = true;
-  int n_ann = 0, one_pos = -1;
-  bool one_edge = false;
-  for (int i = 0; i < 3; i++) {
-    plain = plain && !a.N[i].p && !a.E[i].p;
-    if (a.N[i].p) n_ann++, one_pos = i, one_edge = false;
-    if (a.E[i].p) n_ann++, one_pos = i, one_edge = true;
+__device__ __forceinline__ uint32_t hub_hash(int32_t w) { return (uint32_t)w * 0x9E3779B1u; }
+
+// One CTA per source u in [u_lo, n), highest first.  Shared memory:
+//   acc[R_acc]        u's output row (unary output only), all zero between sources
+//   keys[max_slots]   hash set of N<(u) (-1 = empty), all empty between sources
+//   kpos[max_slots]   index of the key in N<(u) (only when positions are needed)
+// A source with |N<(u)| > max_slots / 2 scans by binary search instead.
+template <int kForm>
+__global__ void __launch_bounds__(kHubThreads) k_triangle_hub(TriArgs a, TriMode md, int32_t u_lo, int max_slots,
+                                                              int R_acc) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  u64 *acc = reinterpret_cast<u64 *>(smem);
+  int32_t *keys = reinterpret_cast<int32_t *>(smem + (size_t)R_acc * 8);
+  uint16_t *kpos = reinterpret_cast<uint16_t *>(keys + max_slots);
+  __shared__ int s_idx;
+  __shared__ u64 s_root;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  unsigned ovf = 0;
+  for (int i = tid; i < max_slots; i += blockDim.x) keys[i] = -1;
+  for (int i = tid; i < R_acc; i += blockDim.x) acc[i] = 0;
+  if (tid == 0) s_root = 0;
+  const int32_t n_hub = (int32_t)(a.g.n - u_lo);
+  while (true) {
+    __syncthreads();  // readers of s_idx and the previous source's clean-up are done
+    if (tid == 0) s_idx = atomicAdd(a.work_counter, 1);
+    __syncthreads();
+    const int idx = s_idx;
+    if (idx >= n_hub) break;
+    const int32_t u = (int32_t)(a.g.n - 1 - idx);
+    const int64_t ub = a.g.row[u];
+    const int du = a.g.lo_cnt[u];
+    if (du < 2) continue;
+    const int cu = a.colors[u];
+    const bool hashed = 2 * du <= max_slots;
+    int slots = 64;
+    if (hashed)
+      while (slots < 2 * du) slots <<= 1;
+    const uint32_t mask = (uint32_t)slots - 1u;
+    const int shift = 32 - __ffs(slots) + 1;  // top log2(slots) bits of the hash
+    if (hashed) {
+      for (int i = tid; i < du; i += blockDim.x) {
+        const int32_t w = __ldg(a.g.col + ub + i);
+        uint32_t h = hub_hash(w) >> shift;
+        for (int t = 0; t < slots; t++, h = (h + 1u) & mask) {
+          if (atomicCAS(keys + h, -1, w) == -1) {
+            if (md.need_pos) kpos[h] = (uint16_t)i;
+            break;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    USink sk;
+    if (a.nb == 1) sk.u = u, sk.acc = acc;
+    u64 root_acc = 0, units = 0;
+    for (int iv = 1 + warp; iv < du; iv += nwarps) {
+      const int32_t v = __ldg(a.g.col + ub + iv);
+      const int dv = a.g.lo_cnt[v];
+      units += (u64)dv;
+      const int cv = a.colors[v];
+      if (cv == cu) continue;
+      const int64_t vb = a.g.row[v];
+      for (int j = lane; j < dv; j += 32) {
+        const int32_t w = __ldg(a.g.col + vb + j);
+        int64_t p = -1;
+        if (hashed) {
+          uint32_t h = hub_hash(w) >> shift;
+          for (int t = 0; t < slots; t++, h = (h + 1u) & mask) {
+            const int32_t kk = keys[h];
+            if (kk == w) {
+              p = md.need_pos ? ub + kpos[h] : 0;
+              break;
+            }
+            if (kk < 0) break;
+          }
+          if (p < 0) continue;
+        } else {
+          p = lower_bound_i32(a.g.col, ub, ub + iv, w);
+          if (p >= ub + iv || __ldg(a.g.col + p) != w) continue;
+        }
+        const int cw = a.colors[w];
+        if (cu == cw || cv == cw) continue;
+        tri_visit<kForm>(a, md, sk, u, v, w, cu, cv, cw, ub + iv, p, vb + j, root_acc, ovf);
+      }
+    }
+    if (a.count_units && lane == 0 && units) atomicAdd(a.status + ST_UNITS, units);
+    if (a.nb == 0) {
+      root_acc = warp_sum_ck(root_acc, ovf);
+      if (lane == 0 && root_acc) atomic_add_ck(&s_root, root_acc, ovf);
+    }
+    __syncthreads();
+    if (a.nb == 0 && tid == 0) {
+      const u64 r = s_root;
+      if (r) {
+        atomic_add_ck(a.status + ST_COUNT, r, ovf);
+        if (a.per_vertex) a.per_vertex[u] = r;
+      }
+      s_root = 0;
+    }
+    if (a.nb == 1) {
+      for (int i = tid; i < R_acc; i += blockDim.x) {
+        const u64 t = acc[i];
+        if (t) {
+          atomic_add_ck(a.out + (int64_t)u * a.R_out + i, t, ovf);
+          acc[i] = 0;
+        }
+      }
+    }
+    if (hashed)
+      for (int i = tid; i < slots; i += blockDim.x) keys[i] = -1;
   }
-  if (n_ann != 1) one_pos = -1;
-  if (cudaMemsetAsync(a.work_counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
-  timing_begin(c, plain ? "triangle_plain" : (one_pos >= 0 ? "triangle_join1" : "triangle_join"));
-  k_triangle<<<152 * 8, 256, 0, c.stream>>>(a, plain, one_pos, one_edge);
+  flag_overflow(a.status, ovf & 1u);
+  if (ovf & 2u) atomicOr(a.status + ST_TIMEOUT, 2ull);  // partial list capacity exceeded
+}
+
+template <int kForm>
+int launch_triangle_form(Ctx &c, const TriArgs &a, const TriMode &md, const char *name) {
+  // sources of degree >= kHubDegree: ranks [u_lo, n) (degree grows with rank)
+  const int64_t n = a.g.n;
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) / 2;
+    if (c.cur_graph_row[mid + 1] - c.cur_graph_row[mid] >= kHubDegree) hi = mid;
+    else lo = mid + 1;
+  }
+  const int32_t u_lo = (int32_t)lo;
+  int max_slots = 64, R_acc = 0;
+  size_t smem = 0;
+  int64_t grid = 0;
+  if (u_lo < n) {
+    const int64_t max_deg = c.cur_graph_row[n] - c.cur_graph_row[n - 1];
+    while (max_slots < kHubMaxSlots && max_slots < 2 * max_deg) max_slots <<= 1;
+    R_acc = a.nb == 1 ? ((a.R_out + 1) & ~1) : 0;
+    smem = (size_t)R_acc * 8 + (size_t)max_slots * (md.need_pos ? 6 : 4);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_triangle_hub<kForm>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return CC_ERR_CUDA;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triangle_hub<kForm>, kHubThreads, smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess)
+      return CC_ERR_CUDA;
+    grid = std::min<int64_t>((int64_t)std::max(per_sm, 1) * sms, n - u_lo);
+  }
+  timing_begin(c, name);
+  if (u_lo < n) {
+    if (cudaMemsetAsync(a.work_counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
+    k_triangle_hub<kForm><<<(int)grid, kHubThreads, smem, c.stream>>>(a, md, u_lo, max_slots, R_acc);
+    c.kernels++;
+    if (cudaGetLastError() != cudaSuccess) return CC_ERR_CUDA;
+  }
+  if (u_lo > 0) {
+    if (cudaMemsetAsync(a.work_counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
+    k_triangle<kForm><<<152 * 8, 256, 0, c.stream>>>(a, md, u_lo);
+    c.kernels++;
+    if (cudaGetLastError() != cudaSuccess) return CC_ERR_CUDA;
+  }
   timing_end(c);
-  return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+  return CC_OK;
+}
+
+int launch_triangle(Ctx &c, const TriArgs &a) {
+  TriMode md;
+  int n_ann = 0;
+  bool any_edge = false;
+  for (int i = 0; i < 3; i++) {
+    md.plain = md.plain && !a.N[i].p && !a.E[i].p;
+    if (a.N[i].p) n_ann++, md.one_pos = i, md.one_edge = false;
+    if (a.E[i].p) n_ann++, md.one_pos = i, md.one_edge = true, any_edge = true;
+  }
+  if (n_ann != 1) md.one_pos = -1;
+  md.need_pos = any_edge || a.nb == 2;
+  if (md.plain) return launch_triangle_form<0>(c, a, md, "triangle_plain");
+  if (md.one_pos >= 0) return launch_triangle_form<1>(c, a, md, "triangle_join1");
+  return launch_triangle_form<2>(c, a, md, "triangle_join");
 }
 
 }  // namespace cc

@@ -112,6 +112,36 @@ def test_heavy_light_split(cc, heavy, qname):
         cc.free_graph(gid)
 
 
+def _wheel_with_chords():
+    # a hub adjacent to all 9000 other vertices (more lower neighbours than
+    # the shared-memory hash holds: the CTA kernel scans it by binary search),
+    # a ring through them and random chords (many hashed sources of degree >= 32)
+    rng = np.random.default_rng(11)
+    n = 9001
+    e = [(0, i) for i in range(1, n)] + [(i, i % 9000 + 1) for i in range(1, n)]
+    e += [tuple(x) for x in rng.integers(1, n, size=(30000, 2)) if x[0] != x[1]]
+    return gg.from_edges(n, np.array(e))
+
+
+@pytest.mark.parametrize("qname", ["triangle", "diamond", "chord_pendant", "tailed_triangle", "bowtie"])
+def test_triangle_sources_of_every_degree(cc, qname):
+    # triangle blocks listed from sources of low degree (one warp each),
+    # hashed hub sources (one CTA each) and a source above the hash capacity
+    import paper_1602_04478_gb300 as P
+    g = _wheel_with_chords()
+    k, e = QUERIES[qname]
+    gid = cc.load_graph(g)
+    try:
+        P.cc_set_coloring_seed(cc.h, 5)
+        qid = cc.set_query(k, e)
+        pv, total = cc.count_per_vertex(gid, qid, 0)
+        expect, _, per = O.dp_count(g, k, e, O.colors(5, 0, g.n, k), per_source=True)
+        assert total == expect
+        assert [int(x) for x in pv] == per
+    finally:
+        cc.free_graph(gid)
+
+
 def test_explicit_colours_and_brute_force(cc):
     import paper_1602_04478_gb300 as P
     g = graph("er60")
