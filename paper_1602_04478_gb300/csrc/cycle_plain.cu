@@ -7,32 +7,39 @@
 //   * level 1 (paths u -> v): membership only; v contributes its colour;
 //   * level 2 (paths u -> v -> w, L = 5, 6): W2[w][c] = number of lower
 //     neighbours v of u adjacent to w with chi(v) = c (chi(w), chi(v),
-//     chi(u) distinct), stored as u32 indexed by colour;
+//     chi(u) distinct);
 //   * at x, over x's neighbours w below u:
-//       A[i]    = number of level-1 neighbours w with free colour i
-//       M[i][j] = sum of W2[w][free j] over level-2 neighbours w with
-//                 free colour i,
-//     so the 3-hop half with free colours {i, j} has M[i][j] + M[j][i]
-//     matches;
-//   * closure (Procedure 2, both halves overlapping only in chi(u), chi(x)):
-//       C4: 2 A[0] A[1]
-//       C5: sum_i A[i] (M[j][l] + M[l][j]),  {i, j, l} = the free colours
-//       C6: 2 sum over the three splits {i,j}|{l,m} of W3[ij] W3[lm].
+//       A[c]     = number of level-1 neighbours w with chi(w) = c
+//       P[{c,d}] = sum of W2[w][d] over level-2 neighbours w with
+//                  chi(w) = c, plus the same with c and d exchanged:
+//                  the 3-hop half u-v-w-x with colours {chi(v), chi(w)}
+//                  = {c, d};
+//   * closure over the free colours (Procedure 2, both halves overlapping
+//     only in chi(u), chi(x)):
+//       C4: 2 A[f0] A[f1]
+//       C5: sum_i A[fi] P[{fj, fl}],  {i, j, l} = {0, 1, 2}
+//       C6: 2 sum over the three splits {i,j}|{l,m} of P[{fi,fj}] P[{fl,fm}].
 // Only one highest node is computed (h = 0) and the total is multiplied by L.
-// Counts at x are accumulated in registers with predicated updates (the
-// free-colour index is data dependent), in 64-bit with overflow checks.
+//
+// Heavy sources run in groups of 32 (lane b of a warp = source b).  Before
+// the groups, every adjacency row is partitioned by neighbour colour (rank
+// order kept inside each colour class) for the colouring at hand, so the
+// pull meets the neighbours of x one colour class at a time: chi(w) is a
+// compile-time index and A, P live in registers.  P entries are exact in
+// 32 bits: a level-2 row entry is below 2^16 and x has fewer than 2^16
+// neighbours (the host checks the maximum degree).
 #include <algorithm>
 
 #include "cc_kernels.h"
 
 namespace cc {
 
-constexpr int kPcMaxB = 16;  // sources per heavy group (one lane each per meeting vertex)
+constexpr int kPcMaxB = 32;  // sources per heavy group (one lane each)
 constexpr int kPcThreads = 256;
 
 struct PcScratch {
-  uint16_t *w2;                // [n][16 sources][8 colours] level-2 rows (u16: max degree < 65536)
-  unsigned long long *member;  // [n]: bit b level 1 of source b, bit 32+b level 2 (b < 16)
+  uint16_t *w2;                // [n][32 sources][8 colours] level-2 rows (u16: max degree < 65536)
+  unsigned long long *member;  // [n]: bit b level 1 of source b, bit 32+b level 2 (b < 32)
   int32_t *list;               // [B][n] level-2 vertices (for clearing)
   int *cnt;                    // [B]
   u64 *totals;                 // [B]
@@ -43,6 +50,55 @@ struct PcGroup {
   int32_t u[kPcMaxB];
   int32_t umax;
 };
+
+// Adjacency partitioned by colour for one colouring: row x of `col` holds
+// x's neighbours grouped by colour (ascending rank within a colour); the
+// class of colour c starts at row offset start[c] (u16 c of off[x]); classes
+// c >= k are empty (start = degree).
+struct ColourAdj {
+  int32_t *col;  // [nnz]
+  uint4 *off;    // [n]: start[0..7]
+};
+
+// One warp per vertex: count the neighbours of each colour with ballots,
+// then scatter each neighbour to its class position (stable).
+__global__ void __launch_bounds__(256) k_colour_adj(GraphView g, const uint8_t *colors, ColourAdj ca) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t x = warp0; x < g.n; x += nwarps) {
+    const int64_t xb = g.row[x];
+    const int deg = (int)(g.row[x + 1] - xb);
+    uint32_t start[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) start[c] = 0;
+    for (int base = 0; base < deg; base += 32) {
+      const int j = base + lane;
+      const int cl = j < deg ? colors[__ldg(g.col + xb + j)] : 8;
+#pragma unroll
+      for (int c = 0; c < 7; c++) start[c + 1] += __popc(__ballot_sync(0xffffffffu, cl == c));
+    }
+#pragma unroll
+    for (int c = 1; c < 8; c++) start[c] += start[c - 1];
+    if (lane == 0)
+      ca.off[x] = make_uint4(start[0] | (start[1] << 16), start[2] | (start[3] << 16), start[4] | (start[5] << 16),
+                             start[6] | (start[7] << 16));
+    for (int base = 0; base < deg; base += 32) {
+      const int j = base + lane;
+      const int32_t w = j < deg ? __ldg(g.col + xb + j) : 0;
+      const int cl = j < deg ? colors[w] : 8;
+      int pos = 0;
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        const unsigned bal = __ballot_sync(0xffffffffu, cl == c);
+        if (cl == c) pos = (int)start[c] + __popc(bal & lt);
+        start[c] += __popc(bal);
+      }
+      if (j < deg) ca.col[xb + pos] = w;
+    }
+  }
+}
 
 // ------------------------------ level build ------------------------------
 // grid.y = source b; warps walk the lower neighbours v of u_b and their
@@ -83,149 +139,132 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uin
 }
 
 // ---------------------------------- pull ----------------------------------
-template <int L>
-struct PcAcc {
-  u64 A[4];
-  u64 M[4][4];
-  __device__ __forceinline__ void zero() {
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-      A[i] = 0;
-#pragma unroll
-      for (int j = 0; j < 4; j++) M[i][j] = 0;
-    }
-  }
-};
-
-// free-colour index of colour c given the two excluded colours (bit mask ex)
-__device__ __forceinline__ int free_idx(int c, uint32_t ex) { return __popc(~ex & ((1u << c) - 1u)); }
-
-template <int L>
-__device__ __forceinline__ void pc_visit(PcAcc<L> &acc, const PcScratch &S, int b, int32_t w, int cw,
-                                         unsigned long long mem, uint32_t ex, uint32_t fm) {
-  if ((ex >> cw) & 1u) return;
-  const int fi = free_idx(cw, ex);
-  constexpr int F = L - 2;
-  if ((L == 4 || L == 5) && ((mem >> b) & 1ull)) {
-#pragma unroll
-    for (int i = 0; i < F; i++) acc.A[i] += (fi == i) ? 1ull : 0ull;
-  }
-  if (L >= 5 && ((mem >> (32 + b)) & 1ull)) {
-    const uint4 rw = __ldg((const uint4 *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8));
-    const uint32_t words[4] = {rw.x, rw.y, rw.z, rw.w};
-    u64 r[4];
-    uint32_t rest = fm;  // free colours, ascending
-#pragma unroll
-    for (int j = 0; j < F; j++) {
-      const int c = __ffs(rest) - 1;
-      rest &= rest - 1;
-      uint32_t wd = (c >> 1) == 0 ? words[0] : (c >> 1) == 1 ? words[1] : (c >> 1) == 2 ? words[2] : words[3];
-      r[j] = (wd >> (16 * (c & 1))) & 0xFFFFu;
-    }
-#pragma unroll
-    for (int i = 0; i < F; i++)
-#pragma unroll
-      for (int j = 0; j < F; j++)
-        if (i != j) acc.M[i][j] += (fi == i) ? r[j] : 0ull;
-  }
+__host__ __device__ constexpr int pc_pair(int a, int b) {  // unordered colour pair, a != b
+  return a > b ? a * (a - 1) / 2 + b : b * (b - 1) / 2 + a;
 }
 
+// One warp per meeting vertex x (below the group's highest source), lane b =
+// source b.  x's colour classes are walked 32 neighbours at a time: each
+// lane loads one neighbour and its membership word, the warp then visits
+// the neighbours that are a member of any source's levels, four at a time
+// (independent level-2 row loads in flight), and each lane adds its own
+// source's row.  The closure at x reads the pair sums through shared memory
+// (the free colours depend on chi(u), which differs per lane).
 template <int L>
-__device__ __forceinline__ u64 pc_close(const PcAcc<L> &acc, unsigned &ovf) {
-  if (L == 4) return mul_ck(2ull, mul_ck(acc.A[0], acc.A[1], ovf), ovf);
-  if (L == 5) {
-    u64 t = 0;
-    t = add_ck(t, mul_ck(acc.A[0], add_ck(acc.M[1][2], acc.M[2][1], ovf), ovf), ovf);
-    t = add_ck(t, mul_ck(acc.A[1], add_ck(acc.M[0][2], acc.M[2][0], ovf), ovf), ovf);
-    t = add_ck(t, mul_ck(acc.A[2], add_ck(acc.M[0][1], acc.M[1][0], ovf), ovf), ovf);
-    return t;
-  }
-  u64 w01 = add_ck(acc.M[0][1], acc.M[1][0], ovf), w23 = add_ck(acc.M[2][3], acc.M[3][2], ovf);
-  u64 w02 = add_ck(acc.M[0][2], acc.M[2][0], ovf), w13 = add_ck(acc.M[1][3], acc.M[3][1], ovf);
-  u64 w03 = add_ck(acc.M[0][3], acc.M[3][0], ovf), w12 = add_ck(acc.M[1][2], acc.M[2][1], ovf);
-  u64 t = add_ck(add_ck(mul_ck(w01, w23, ovf), mul_ck(w02, w13, ovf), ovf), mul_ck(w03, w12, ovf), ovf);
-  return mul_ck(2ull, t, ovf);
-}
-
-// sum a value over the two lanes that share this lane's source (lanes b, b+16)
-__device__ __forceinline__ u64 pc_sum4(u64 v, unsigned &ovf) {
-  return add_ck(v, __shfl_xor_sync(0xffffffffu, v, 16), ovf);
-}
-
-template <int L>
-__device__ __forceinline__ void pc_reduce4(PcAcc<L> &acc, unsigned &ovf) {
-  constexpr int F = L - 2;
-#pragma unroll
-  for (int i = 0; i < F; i++) {
-    if (L <= 5) acc.A[i] = pc_sum4(acc.A[i], ovf);
-#pragma unroll
-    for (int j = 0; j < F; j++)
-      if (L >= 5 && i != j) acc.M[i][j] = pc_sum4(acc.M[i][j], ovf);
-  }
-}
-
-// Lane (q, b) of a warp: b = lane & 15 is the source, q = lane >> 4 picks
-// one of two meeting vertices (low degree) or half of one vertex's
-// neighbours (high degree).  The 16 lanes of a vertex read the same neighbour
-// ids and membership words, and adjacent level-2 rows.
-template <int L>
-__global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const uint8_t *colors, PcScratch S, PcGroup G,
-                                                        int32_t x_split, int k) {
-  const int lane = threadIdx.x & 31;
-  const int b = lane & 15, q = lane >> 4;
+__global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const uint8_t *colors, ColourAdj ca,
+                                                        PcScratch S, PcGroup G, u64 *status) {
+  constexpr int NP = L * (L - 1) / 2;
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ uint32_t sP[L >= 5 ? NP : 1][kPcThreads];
+  __shared__ uint32_t sA[L <= 5 ? L : 1][kPcThreads];
+  const int tid = threadIdx.x, lane = tid & 31, b = lane;
   const bool active = b < G.B;
   const int32_t ub = active ? G.u[b] : -1;
-  const int cu = active ? colors[ub] : 0;
+  const int cu = active ? colors[ub] : -1;
+  const int32_t umax = G.umax;
   u64 tot = 0;
   unsigned ovf = 0;
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // low-degree meeting vertices: two per warp
-  const int32_t lo_end = min(x_split, G.umax);
-  for (int64_t x0 = warp0 * 2; x0 < lo_end; x0 += nwarps * 2) {
-    const int32_t x = (int32_t)(x0 + q);
-    if (x >= lo_end || !active || x >= ub) continue;
-    const int cx = colors[x];
-    if (cx == cu) continue;
-    const uint32_t ex = (1u << cu) | (1u << cx);
-    const uint32_t fm = ~ex & ((1u << k) - 1u);
-    PcAcc<L> acc;
-    acc.zero();
-    const int64_t xb = g.row[x], xe = g.row[x + 1];
-    for (int64_t e = xb; e < xe; e++) {
-      const int32_t w = __ldg(g.col + e);
-      if (w >= ub) break;
-      const unsigned long long mem = __ldg(S.member + w);
-      if (!((mem >> b) & 0x100000001ull)) continue;
-      pc_visit<L>(acc, S, b, w, colors[w], mem, ex, fm);
-    }
-    tot = add_ck(tot, pc_close<L>(acc, ovf), ovf);
-  }
-  // high-degree meeting vertices: one warp each, half of the neighbours per lane
-  for (int64_t xi = (int64_t)x_split + warp0; xi < G.umax; xi += nwarps) {
+  for (int64_t xi = warp0; xi < umax; xi += nwarps) {
     const int32_t x = (int32_t)xi;
     const int cx = colors[x];
-    const bool ok = active && x < ub && cx != cu;
-    const uint32_t ex = (1u << cu) | (1u << cx);
-    const uint32_t fm = ~ex & ((1u << k) - 1u);
-    PcAcc<L> acc;
-    acc.zero();
-    if (ok) {
-      const int64_t xb = g.row[x], xe = g.row[x + 1];
-      for (int64_t e = xb + q; e < xe; e += 2) {
-        const int32_t w = __ldg(g.col + e);
-        if (w >= ub) break;
-        const unsigned long long mem = __ldg(S.member + w);
-        if (!((mem >> b) & 0x100000001ull)) continue;
-        pc_visit<L>(acc, S, b, w, colors[w], mem, ex, fm);
+    const bool act = active && x < ub && cx != cu;
+    if (!__any_sync(FULL, act)) continue;
+    const int64_t xb = g.row[x];
+    const uint4 o4 = __ldg(ca.off + x);
+    const uint32_t ow[4] = {o4.x, o4.y, o4.z, o4.w};
+    uint32_t A[L], P[L >= 5 ? NP : 1];
+#pragma unroll
+    for (int c = 0; c < L; c++) A[c] = 0;
+#pragma unroll
+    for (int j = 0; j < (L >= 5 ? NP : 1); j++) P[j] = 0;
+    bool hit = false;
+#pragma unroll
+    for (int c = 0; c < L; c++) {
+      if (c == cx) continue;  // chi(w) = chi(x) closes no colourful cycle
+      const int s = (ow[c >> 1] >> (16 * (c & 1))) & 0xFFFF;
+      const int e = (ow[(c + 1) >> 1] >> (16 * ((c + 1) & 1))) & 0xFFFF;
+      const bool take = act && c != cu;
+      for (int base = s; base < e; base += 32) {
+        const int j = base + lane;
+        const int32_t wl = j < e ? __ldg(ca.col + xb + j) : INT32_MAX;
+        const unsigned long long ml = wl < umax ? __ldg(S.member + wl) : 0ull;
+        unsigned m = __ballot_sync(FULL, ml != 0ull);
+        // the class is rank ordered: past the highest source, nothing further counts
+        const bool past = __any_sync(FULL, wl >= umax);
+        while (m) {
+          int32_t ww[4];
+          unsigned long long mm[4];
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const int t = m ? __ffs(m) - 1 : 0;
+            const bool valid = m != 0u;
+            m &= m - 1u;
+            ww[q] = __shfl_sync(FULL, wl, t);
+            const unsigned long long mt = __shfl_sync(FULL, ml, t);
+            mm[q] = valid ? mt : 0ull;
+          }
+          uint4 rr[4];
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const bool in = take && ww[q] < ub;
+            if (L <= 5 && in && ((mm[q] >> b) & 1ull)) {
+              A[c] += 1u;
+              hit = true;
+            }
+            rr[q] = make_uint4(0, 0, 0, 0);
+            if (L >= 5 && in && ((mm[q] >> (32 + b)) & 1ull)) {
+              rr[q] = __ldg((const uint4 *)(S.w2 + ((int64_t)ww[q] * kPcMaxB + b) * 8));
+              hit = true;
+            }
+          }
+          if (L >= 5) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+              const uint32_t wd[4] = {rr[q].x, rr[q].y, rr[q].z, rr[q].w};
+#pragma unroll
+              for (int d = 0; d < L; d++)
+                if (d != c) P[pc_pair(c, d)] += (wd[d >> 1] >> (16 * (d & 1))) & 0xFFFFu;
+            }
+          }
+        }
+        if (past) break;
       }
     }
-    pc_reduce4<L>(acc, ovf);
-    if (ok && q == 0) tot = add_ck(tot, pc_close<L>(acc, ovf), ovf);
+    if (!act || !hit) continue;
+    // free colours f0 < f1 < ... (all but chi(u) and chi(x))
+    uint32_t rest = ((1u << L) - 1u) & ~((1u << cu) | (1u << cx));
+    int f[4];
+#pragma unroll
+    for (int i = 0; i < L - 2; i++) {
+      f[i] = __ffs(rest) - 1;
+      rest &= rest - 1u;
+    }
+    if (L <= 5) {
+#pragma unroll
+      for (int c = 0; c < L; c++) sA[c][tid] = A[c];
+    }
+    if (L >= 5) {
+#pragma unroll
+      for (int j = 0; j < NP; j++) sP[j][tid] = P[j];
+    }
+    if (L == 4) {
+      tot = add_ck(tot, mul_ck(2ull, mul_ck(sA[f[0]][tid], sA[f[1]][tid], ovf), ovf), ovf);
+    } else if (L == 5) {
+      u64 t = mul_ck(sA[f[0]][tid], sP[pc_pair(f[1], f[2])][tid], ovf);
+      t = add_ck(t, mul_ck(sA[f[1]][tid], sP[pc_pair(f[0], f[2])][tid], ovf), ovf);
+      t = add_ck(t, mul_ck(sA[f[2]][tid], sP[pc_pair(f[0], f[1])][tid], ovf), ovf);
+      tot = add_ck(tot, t, ovf);
+    } else {
+      u64 t = (u64)sP[pc_pair(f[0], f[1])][tid] * sP[pc_pair(f[2], f[3])][tid];
+      t = add_ck(t, (u64)sP[pc_pair(f[0], f[2])][tid] * sP[pc_pair(f[1], f[3])][tid], ovf);
+      t = add_ck(t, (u64)sP[pc_pair(f[0], f[3])][tid] * sP[pc_pair(f[1], f[2])][tid], ovf);
+      tot = add_ck(tot, mul_ck(2ull, t, ovf), ovf);
+    }
   }
-  tot = pc_sum4(tot, ovf);
-  if (q == 0 && active && tot) atomic_add_ck(S.totals + b, tot, ovf);
-  (void)ovf;
+  if (active && tot) atomic_add_ck(S.totals + b, tot, ovf);
+  flag_overflow(status, ovf);
 }
 
 // --------------------------- clear and finish ---------------------------
@@ -485,9 +524,11 @@ int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank) {
 }
 
 template <int L>
-static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, int32_t x_split, const PcScratch &S) {
+static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const ColourAdj &ca, const PcScratch &S) {
   const int64_t n = a.g.n;
   const int sms = 152;
+  k_colour_adj<<<sms * 8, 256, 0, c.stream>>>(a.g, a.colors, ca);
+  c.kernels++;
   for (int64_t top = n - 1; top >= first_rank; top -= kPcMaxB) {
     PcGroup G;
     G.B = (int)std::min<int64_t>(kPcMaxB, top - first_rank + 1);
@@ -501,7 +542,7 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, int32_t x
     c.kernels++;
     timing_end(c);
     timing_begin(c, "cycle_plain_pull");
-    k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G, x_split, a.k);
+    k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, ca, S, G, a.status);
     c.kernels++;
     timing_end(c);
     k_pc_clear<L><<<sms, 256, 0, c.stream>>>(a.g, a.colors, S, G);
@@ -534,6 +575,8 @@ int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank) {
   size_t o_list = lv2 ? take((size_t)kPcMaxB * n * 4) : 0;
   size_t o_cnt = take(kPcMaxB * 4);
   size_t o_tot = take(kPcMaxB * 8);
+  size_t o_ccol = take((size_t)std::max<int64_t>(a.g.nnz, 1) * 4);
+  size_t o_coff = take((size_t)n * 16);
   size_t need = off;
   int rc0 = ensure_hv_scratch(c, need);
   if (rc0 != CC_OK) return rc0;
@@ -544,16 +587,12 @@ int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank) {
   S.list = (int32_t *)(base + o_list);
   S.cnt = (int *)(base + o_cnt);
   S.totals = (u64 *)(base + o_tot);
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) / 2;
-    if (c.cur_graph_row[mid + 1] - c.cur_graph_row[mid] >= 32) hi = mid;
-    else lo = mid + 1;
-  }
-  const int32_t x_split = (int32_t)lo;
-  if (a.L == 4) return run_plain_L<4>(c, a, first_rank, x_split, S);
-  if (a.L == 5) return run_plain_L<5>(c, a, first_rank, x_split, S);
-  return run_plain_L<6>(c, a, first_rank, x_split, S);
+  ColourAdj ca;
+  ca.col = (int32_t *)(base + o_ccol);
+  ca.off = (uint4 *)(base + o_coff);
+  if (a.L == 4) return run_plain_L<4>(c, a, first_rank, ca, S);
+  if (a.L == 5) return run_plain_L<5>(c, a, first_rank, ca, S);
+  return run_plain_L<6>(c, a, first_rank, ca, S);
 }
 
 }  // namespace cc
