@@ -575,8 +575,6 @@ int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank) {
   size_t o_list = lv2 ? take((size_t)kPcMaxB * n * 4) : 0;
   size_t o_cnt = take(kPcMaxB * 4);
   size_t o_tot = take(kPcMaxB * 8);
-  size_t o_ccol = take((size_t)std::max<int64_t>(a.g.nnz, 1) * 4);
-  size_t o_coff = take((size_t)n * 16);
   size_t need = off;
   int rc0 = ensure_hv_scratch(c, need);
   if (rc0 != CC_OK) return rc0;
@@ -587,9 +585,13 @@ int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank) {
   S.list = (int32_t *)(base + o_list);
   S.cnt = (int *)(base + o_cnt);
   S.totals = (u64 *)(base + o_tot);
+  // the colour-partitioned adjacency is not zero: it lives outside the
+  // heavy scratch, whose layout changes with the graph
+  const size_t ccol_bytes = ((size_t)std::max<int64_t>(a.g.nnz, 1) * 4 + 255) & ~(size_t)255;
+  if ((rc0 = ensure_adj_scratch(c, ccol_bytes + (size_t)n * 16)) != CC_OK) return rc0;
   ColourAdj ca;
-  ca.col = (int32_t *)(base + o_ccol);
-  ca.off = (uint4 *)(base + o_coff);
+  ca.col = (int32_t *)c.adj_scratch;
+  ca.off = (uint4 *)((char *)c.adj_scratch + ccol_bytes);
   if (a.L == 4) return run_plain_L<4>(c, a, first_rank, ca, S);
   if (a.L == 5) return run_plain_L<5>(c, a, first_rank, ca, S);
   return run_plain_L<6>(c, a, first_rank, ca, S);

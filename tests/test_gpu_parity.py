@@ -142,6 +142,30 @@ def test_triangle_sources_of_every_degree(cc, qname):
         cc.free_graph(gid)
 
 
+def test_scratch_reuse_across_graphs_and_queries(cc):
+    # one context counts different graphs and cycle lengths in turn, every
+    # source on the heavy path: scratch left by one (graph, query) must not
+    # leak into the next, whose layout differs
+    import paper_1602_04478_gb300 as P
+    seq = [("er60", "C6"), ("cl3000", "C5"), ("er2000", "C6"), ("rmat10", "C4"), ("cl3000", "C6"), ("er60", "C5")]
+    P.cc_set_heavy_degree(cc.h, 0)
+    try:
+        for gname, qname in seq:
+            g = graph(gname)
+            k, e = QUERIES[qname]
+            gid = cc.load_graph(g)
+            try:
+                P.cc_set_coloring_seed(cc.h, 13)
+                qid = cc.set_query(k, e)
+                col, _, _ = cc.count(gid, qid, 0, 1)
+                expect, _ = O.dp_count(g, k, e, O.colors(13, 0, g.n, k))
+                assert int(col[0]) == expect, (gname, qname)
+            finally:
+                cc.free_graph(gid)
+    finally:
+        P.cc_set_heavy_degree(cc.h, -1)
+
+
 def test_explicit_colours_and_brute_force(cc):
     import paper_1602_04478_gb300 as P
     g = graph("er60")
