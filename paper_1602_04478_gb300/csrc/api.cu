@@ -59,7 +59,6 @@ int ensure_hv_scratch(Ctx &c, size_t bytes) {
     if (c.hv_scratch) {
       cudaStreamSynchronize(c.stream);
       dev_free(c, c.hv_scratch, c.hv_scratch_bytes);
-  dev_free(c, c.adj_scratch, c.adj_scratch_bytes);
     }
     c.hv_scratch = dev_alloc(c, bytes);
     c.hv_scratch_bytes = c.hv_scratch ? bytes : 0;
