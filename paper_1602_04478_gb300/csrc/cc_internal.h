@@ -89,8 +89,6 @@ struct Ctx {
   unsigned epoch = 0;
   void *hv_scratch = nullptr;    // heavy-source cycle scratch (all zero between launches)
   size_t hv_scratch_bytes = 0;
-  void *adj_scratch = nullptr;   // per-colouring derived arrays, rewritten before use (no zero invariant)
-  size_t adj_scratch_bytes = 0;
   bool hv_dirty = true;
   const int64_t *cur_graph_row = nullptr;  // host row pointers of the graph being counted
   int heavy_degree = -1;         // sources of at least this degree take the heavy path (-1: tuned / default)
@@ -110,7 +108,6 @@ void *dev_alloc(Ctx &c, size_t bytes);
 void dev_free(Ctx &c, void *p, size_t bytes);
 int ensure_scratch(Ctx &c, size_t bytes);
 int ensure_hv_scratch(Ctx &c, size_t bytes);  // grows and, when fresh or dirty, zeroes the heavy scratch
-int ensure_adj_scratch(Ctx &c, size_t bytes); // grows only
 
 // kernel-launch bracketing for the optional timing
 void batch_cache_clear(Ctx &c);  // drop captured batch graphs and their buffers

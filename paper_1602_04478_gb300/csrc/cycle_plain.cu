@@ -21,13 +21,10 @@
 //       C6: 2 sum over the three splits {i,j}|{l,m} of P[{fi,fj}] P[{fl,fm}].
 // Only one highest node is computed (h = 0) and the total is multiplied by L.
 //
-// Heavy sources run in groups of 32 (lane b of a warp = source b).  Before
-// the groups, every adjacency row is partitioned by neighbour colour (rank
-// order kept inside each colour class) for the colouring at hand, so the
-// pull meets the neighbours of x one colour class at a time: chi(w) is a
-// compile-time index and A, P live in registers.  P entries are exact in
-// 32 bits: a level-2 row entry is below 2^16 and x has fewer than 2^16
-// neighbours (the host checks the maximum degree).
+// Heavy sources run in groups of 32 (lane b of a warp = source b); A and P
+// live in registers.  P entries are exact in 32 bits: a level-2 row entry is
+// below 2^16 and x has fewer than 2^16 neighbours (the host checks the
+// maximum degree).
 #include <algorithm>
 
 #include "cc_kernels.h"
@@ -50,55 +47,6 @@ struct PcGroup {
   int32_t u[kPcMaxB];
   int32_t umax;
 };
-
-// Adjacency partitioned by colour for one colouring: row x of `col` holds
-// x's neighbours grouped by colour (ascending rank within a colour); the
-// class of colour c starts at row offset start[c] (u16 c of off[x]); classes
-// c >= k are empty (start = degree).
-struct ColourAdj {
-  int32_t *col;  // [nnz]
-  uint4 *off;    // [n]: start[0..7]
-};
-
-// One warp per vertex: count the neighbours of each colour with ballots,
-// then scatter each neighbour to its class position (stable).
-__global__ void __launch_bounds__(256) k_colour_adj(GraphView g, const uint8_t *colors, ColourAdj ca) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t x = warp0; x < g.n; x += nwarps) {
-    const int64_t xb = g.row[x];
-    const int deg = (int)(g.row[x + 1] - xb);
-    uint32_t start[8];
-#pragma unroll
-    for (int c = 0; c < 8; c++) start[c] = 0;
-    for (int base = 0; base < deg; base += 32) {
-      const int j = base + lane;
-      const int cl = j < deg ? colors[__ldg(g.col + xb + j)] : 8;
-#pragma unroll
-      for (int c = 0; c < 7; c++) start[c + 1] += __popc(__ballot_sync(0xffffffffu, cl == c));
-    }
-#pragma unroll
-    for (int c = 1; c < 8; c++) start[c] += start[c - 1];
-    if (lane == 0)
-      ca.off[x] = make_uint4(start[0] | (start[1] << 16), start[2] | (start[3] << 16), start[4] | (start[5] << 16),
-                             start[6] | (start[7] << 16));
-    for (int base = 0; base < deg; base += 32) {
-      const int j = base + lane;
-      const int32_t w = j < deg ? __ldg(g.col + xb + j) : 0;
-      const int cl = j < deg ? colors[w] : 8;
-      int pos = 0;
-#pragma unroll
-      for (int c = 0; c < 8; c++) {
-        const unsigned bal = __ballot_sync(0xffffffffu, cl == c);
-        if (cl == c) pos = (int)start[c] + __popc(bal & lt);
-        start[c] += __popc(bal);
-      }
-      if (j < deg) ca.col[xb + pos] = w;
-    }
-  }
-}
 
 // ------------------------------ level build ------------------------------
 // grid.y = source b; warps walk the lower neighbours v of u_b and their
@@ -129,10 +77,15 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uin
       if (cw == cu || cw == cv) continue;
       // 16-bit counter inside a 32-bit word; counts stay below 2^16 (host check)
       atomicAdd((uint32_t *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8 + (cv & ~1)), 1u << (16 * (cv & 1)));
-      unsigned long long old = atomicOr(S.member + w, 1ull << (32 + b));
-      if (!((old >> (32 + b)) & 1ull)) {
-        int slot = atomicAdd(S.cnt + b, 1);
-        S.list[(int64_t)b * n + slot] = w;
+      // bits are only set during this kernel, so a stale read can only miss
+      // one and cost a redundant atomic; the atomic's old value decides
+      // which thread lists w
+      if (!((__ldcg(S.member + w) >> (32 + b)) & 1ull)) {
+        unsigned long long old = atomicOr(S.member + w, 1ull << (32 + b));
+        if (!((old >> (32 + b)) & 1ull)) {
+          int slot = atomicAdd(S.cnt + b, 1);
+          S.list[(int64_t)b * n + slot] = w;
+        }
       }
     }
   }
@@ -143,16 +96,47 @@ __host__ __device__ constexpr int pc_pair(int a, int b) {  // unordered colour p
   return a > b ? a * (a - 1) / 2 + b : b * (b - 1) / 2 + a;
 }
 
+// Accumulate one level-2 row (w of colour c) into the pair sums:
+// P[{c, d}] += W2[w][d] for every colour d != c.  c is a compile-time index.
+template <int L, int c>
+__device__ __forceinline__ void pc_add_row(uint32_t (&P)[L * (L - 1) / 2], const uint4 &r) {
+  const uint32_t wd[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+  for (int d = 0; d < L; d++)
+    if (d != c) P[pc_pair(c, d)] += (wd[d >> 1] >> (16 * (d & 1))) & 0xFFFFu;
+}
+
+template <int L>
+__device__ __forceinline__ void pc_add_row_dyn(uint32_t (&P)[L * (L - 1) / 2], const uint4 &r, int c) {
+  // c is the same in every lane of the warp: the branch does not diverge
+  switch (c) {
+    case 0: pc_add_row<L, 0>(P, r); break;
+    case 1: pc_add_row<L, 1>(P, r); break;
+    case 2: pc_add_row<L, 2>(P, r); break;
+    case 3: pc_add_row<L, 3>(P, r); break;
+    case 4: if (L > 4) pc_add_row<L, (L > 4 ? 4 : 0)>(P, r); break;
+    default: if (L > 5) pc_add_row<L, (L > 5 ? 5 : 0)>(P, r); break;
+  }
+}
+
+template <int L>
+__device__ __forceinline__ void pc_add_one(uint32_t (&A)[L], int c, uint32_t v) {
+#pragma unroll
+  for (int i = 0; i < L; i++) A[i] += (c == i) ? v : 0u;
+}
+
 // One warp per meeting vertex x (below the group's highest source), lane b =
-// source b.  x's colour classes are walked 32 neighbours at a time: each
-// lane loads one neighbour and its membership word, the warp then visits
-// the neighbours that are a member of any source's levels, four at a time
-// (independent level-2 row loads in flight), and each lane adds its own
-// source's row.  The closure at x reads the pair sums through shared memory
+// source b.  x's neighbours are read 32 at a time: each lane loads one
+// neighbour, its colour and its membership word; the warp then visits the
+// neighbours that belong to any source's levels, four at a time (their
+// level-2 row loads in flight together), and each lane adds its own
+// source's row.  The visited neighbour's colour is the same in all lanes,
+// so a switch on it selects compile-time register indices without
+// divergence.  The closure at x reads the pair sums through shared memory
 // (the free colours depend on chi(u), which differs per lane).
 template <int L>
-__global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const uint8_t *colors, ColourAdj ca,
-                                                        PcScratch S, PcGroup G, u64 *status) {
+__global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const uint8_t *colors, PcScratch S,
+                                                        PcGroup G, u64 *status) {
   constexpr int NP = L * (L - 1) / 2;
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ uint32_t sP[L >= 5 ? NP : 1][kPcThreads];
@@ -172,65 +156,57 @@ __global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const ui
     const bool act = active && x < ub && cx != cu;
     if (!__any_sync(FULL, act)) continue;
     const int64_t xb = g.row[x];
-    const uint4 o4 = __ldg(ca.off + x);
-    const uint32_t ow[4] = {o4.x, o4.y, o4.z, o4.w};
-    uint32_t A[L], P[L >= 5 ? NP : 1];
+    const int deg = (int)(g.row[x + 1] - xb);
+    uint32_t A[L], P[NP];
 #pragma unroll
     for (int c = 0; c < L; c++) A[c] = 0;
 #pragma unroll
-    for (int j = 0; j < (L >= 5 ? NP : 1); j++) P[j] = 0;
+    for (int j = 0; j < NP; j++) P[j] = 0;
     bool hit = false;
+    for (int base = 0; base < deg; base += 32) {
+      const int j = base + lane;
+      const int32_t wl = j < deg ? __ldg(g.col + xb + j) : INT32_MAX;
+      // the row is rank ordered: past the highest source, nothing further counts
+      const bool past = __any_sync(FULL, wl >= umax);
+      const int cl = wl < umax ? colors[wl] : cx;
+      // chi(w) = chi(x) closes no colourful cycle
+      const unsigned long long ml = cl != cx ? __ldg(S.member + wl) : 0ull;
+      unsigned m = __ballot_sync(FULL, ml != 0ull);
+      while (m) {
+        int32_t ww[4];
+        int cc[4];
+        unsigned long long mm[4];
 #pragma unroll
-    for (int c = 0; c < L; c++) {
-      if (c == cx) continue;  // chi(w) = chi(x) closes no colourful cycle
-      const int s = (ow[c >> 1] >> (16 * (c & 1))) & 0xFFFF;
-      const int e = (ow[(c + 1) >> 1] >> (16 * ((c + 1) & 1))) & 0xFFFF;
-      const bool take = act && c != cu;
-      for (int base = s; base < e; base += 32) {
-        const int j = base + lane;
-        const int32_t wl = j < e ? __ldg(ca.col + xb + j) : INT32_MAX;
-        const unsigned long long ml = wl < umax ? __ldg(S.member + wl) : 0ull;
-        unsigned m = __ballot_sync(FULL, ml != 0ull);
-        // the class is rank ordered: past the highest source, nothing further counts
-        const bool past = __any_sync(FULL, wl >= umax);
-        while (m) {
-          int32_t ww[4];
-          unsigned long long mm[4];
+        for (int q = 0; q < 4; q++) {
+          const int t = m ? __ffs(m) - 1 : 0;
+          const bool valid = m != 0u;
+          m &= m - 1u;
+          ww[q] = __shfl_sync(FULL, wl, t);
+          cc[q] = valid ? __shfl_sync(FULL, cl, t) : -1;
+          const unsigned long long mt = __shfl_sync(FULL, ml, t);
+          mm[q] = valid ? mt : 0ull;
+        }
+        uint4 rr[4];
 #pragma unroll
-          for (int q = 0; q < 4; q++) {
-            const int t = m ? __ffs(m) - 1 : 0;
-            const bool valid = m != 0u;
-            m &= m - 1u;
-            ww[q] = __shfl_sync(FULL, wl, t);
-            const unsigned long long mt = __shfl_sync(FULL, ml, t);
-            mm[q] = valid ? mt : 0ull;
+        for (int q = 0; q < 4; q++) {
+          const bool in = act && ww[q] < ub && cc[q] != cu;
+          if (L <= 5 && in && ((mm[q] >> b) & 1ull)) {
+            pc_add_one<L>(A, cc[q], 1u);
+            hit = true;
           }
-          uint4 rr[4];
-#pragma unroll
-          for (int q = 0; q < 4; q++) {
-            const bool in = take && ww[q] < ub;
-            if (L <= 5 && in && ((mm[q] >> b) & 1ull)) {
-              A[c] += 1u;
-              hit = true;
-            }
-            rr[q] = make_uint4(0, 0, 0, 0);
-            if (L >= 5 && in && ((mm[q] >> (32 + b)) & 1ull)) {
-              rr[q] = __ldg((const uint4 *)(S.w2 + ((int64_t)ww[q] * kPcMaxB + b) * 8));
-              hit = true;
-            }
-          }
-          if (L >= 5) {
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-              const uint32_t wd[4] = {rr[q].x, rr[q].y, rr[q].z, rr[q].w};
-#pragma unroll
-              for (int d = 0; d < L; d++)
-                if (d != c) P[pc_pair(c, d)] += (wd[d >> 1] >> (16 * (d & 1))) & 0xFFFFu;
-            }
+          rr[q] = make_uint4(0, 0, 0, 0);
+          if (L >= 5 && in && ((mm[q] >> (32 + b)) & 1ull)) {
+            rr[q] = __ldg((const uint4 *)(S.w2 + ((int64_t)ww[q] * kPcMaxB + b) * 8));
+            hit = true;
           }
         }
-        if (past) break;
+        if (L >= 5) {
+#pragma unroll
+          for (int q = 0; q < 4; q++)
+            if (cc[q] >= 0) pc_add_row_dyn<L>(P, rr[q], cc[q]);
+        }
       }
+      if (past) break;
     }
     if (!act || !hit) continue;
     // free colours f0 < f1 < ... (all but chi(u) and chi(x))
@@ -524,11 +500,9 @@ int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank) {
 }
 
 template <int L>
-static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const ColourAdj &ca, const PcScratch &S) {
+static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcScratch &S) {
   const int64_t n = a.g.n;
   const int sms = 152;
-  k_colour_adj<<<sms * 8, 256, 0, c.stream>>>(a.g, a.colors, ca);
-  c.kernels++;
   for (int64_t top = n - 1; top >= first_rank; top -= kPcMaxB) {
     PcGroup G;
     G.B = (int)std::min<int64_t>(kPcMaxB, top - first_rank + 1);
@@ -542,7 +516,7 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const Col
     c.kernels++;
     timing_end(c);
     timing_begin(c, "cycle_plain_pull");
-    k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, ca, S, G, a.status);
+    k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G, a.status);
     c.kernels++;
     timing_end(c);
     k_pc_clear<L><<<sms, 256, 0, c.stream>>>(a.g, a.colors, S, G);
@@ -585,16 +559,9 @@ int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank) {
   S.list = (int32_t *)(base + o_list);
   S.cnt = (int *)(base + o_cnt);
   S.totals = (u64 *)(base + o_tot);
-  // the colour-partitioned adjacency is not zero: it lives outside the
-  // heavy scratch, whose layout changes with the graph
-  const size_t ccol_bytes = ((size_t)std::max<int64_t>(a.g.nnz, 1) * 4 + 255) & ~(size_t)255;
-  if ((rc0 = ensure_adj_scratch(c, ccol_bytes + (size_t)n * 16)) != CC_OK) return rc0;
-  ColourAdj ca;
-  ca.col = (int32_t *)c.adj_scratch;
-  ca.off = (uint4 *)((char *)c.adj_scratch + ccol_bytes);
-  if (a.L == 4) return run_plain_L<4>(c, a, first_rank, ca, S);
-  if (a.L == 5) return run_plain_L<5>(c, a, first_rank, ca, S);
-  return run_plain_L<6>(c, a, first_rank, ca, S);
+  if (a.L == 4) return run_plain_L<4>(c, a, first_rank, S);
+  if (a.L == 5) return run_plain_L<5>(c, a, first_rank, S);
+  return run_plain_L<6>(c, a, first_rank, S);
 }
 
 }  // namespace cc
