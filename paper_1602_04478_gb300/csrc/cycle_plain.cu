@@ -50,10 +50,13 @@ struct PcGroup {
 
 // ------------------------------ level build ------------------------------
 // grid.y = source b; warps walk the lower neighbours v of u_b and their
-// neighbours w below u_b.
+// neighbours w below u_b, 32 at a time (v's row is rank ordered, so the walk
+// stops at the first chunk that reaches u_b).  A level-2 vertex is listed
+// once per source, the warp taking its list slots with one atomic.
 template <int L>
 __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uint8_t *colors, PcScratch S,
                                                           PcGroup G) {
+  constexpr unsigned FULL = 0xffffffffu;
   const int b = blockIdx.y;
   const int32_t u = G.u[b];
   const int cu = colors[u];
@@ -61,6 +64,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uin
   const int64_t ub = g.row[u];
   const int du = g.lo_cnt[u];
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp0; i < du; i += nwarps) {
@@ -69,24 +73,35 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uin
     if (cv == cu) continue;
     if (L <= 5 && lane == 0) atomicOr(S.member + v, 1ull << b);
     if (L == 4) continue;
-    const int64_t vb = g.row[v];
-    const int64_t ve = lower_bound_i32(g.col, vb, g.row[v + 1], u);
-    for (int64_t e = vb + lane; e < ve; e += 32) {
-      const int32_t w = __ldg(g.col + e);
-      const int cw = colors[w];
-      if (cw == cu || cw == cv) continue;
-      // 16-bit counter inside a 32-bit word; counts stay below 2^16 (host check)
-      atomicAdd((uint32_t *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8 + (cv & ~1)), 1u << (16 * (cv & 1)));
-      // bits are only set during this kernel, so a stale read can only miss
-      // one and cost a redundant atomic; the atomic's old value decides
-      // which thread lists w
-      if (!((__ldcg(S.member + w) >> (32 + b)) & 1ull)) {
-        unsigned long long old = atomicOr(S.member + w, 1ull << (32 + b));
-        if (!((old >> (32 + b)) & 1ull)) {
-          int slot = atomicAdd(S.cnt + b, 1);
-          S.list[(int64_t)b * n + slot] = w;
+    const int64_t vb = g.row[v], vend = g.row[v + 1];
+    for (int64_t e0 = vb; e0 < vend; e0 += 32) {
+      const int64_t e = e0 + lane;
+      const int32_t w = e < vend ? __ldg(g.col + e) : INT32_MAX;
+      const bool done = __any_sync(FULL, w >= u);
+      bool need = false;
+      if (w < u) {
+        const int cw = colors[w];
+        if (cw != cu && cw != cv) {
+          // 16-bit counter inside a 32-bit word; counts stay below 2^16 (host check)
+          atomicAdd((uint32_t *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8 + (cv & ~1)), 1u << (16 * (cv & 1)));
+          // bits are only set during this kernel, so a stale read can only
+          // miss one and cost a redundant atomic; the atomic's old value
+          // decides which thread lists w
+          if (!((__ldcg(S.member + w) >> (32 + b)) & 1ull)) {
+            const unsigned long long old = atomicOr(S.member + w, 1ull << (32 + b));
+            need = !((old >> (32 + b)) & 1ull);
+          }
         }
       }
+      const unsigned nb = __ballot_sync(FULL, need);
+      if (nb) {
+        const int leader = __ffs(nb) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(S.cnt + b, __popc(nb));
+        base = __shfl_sync(FULL, base, leader);
+        if (need) S.list[(int64_t)b * n + base + __popc(nb & lt)] = w;
+      }
+      if (done) break;
     }
   }
 }
