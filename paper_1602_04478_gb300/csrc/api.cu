@@ -202,6 +202,7 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
   Lut lut{c.lut_rank, c.lut_unrank};
   GraphView gv = view_of(g);
   c.cur_graph_row = g.h_row.data();
+  c.cur_graph = &g;
   std::vector<Table> &T = B.T;
   for (size_t i = 0; i < p.stages.size() && rc == CC_OK; i++) {
     const Stage &st = p.stages[i];

@@ -64,6 +64,7 @@ struct DevGraph {
   std::vector<int64_t> h_row;  // host copy of the relabelled row pointers
   std::map<int, double> work_cache;  // query id -> structural work units
   std::map<int, int> tuned_heavy;    // query id -> heavy-source degree threshold (autotuned)
+  std::vector<int64_t> h_push_work;  // per rank u: pairs (v, w), v in N<(u), w in N(v), w < u (empty: not yet)
 };
 
 // -------------------------------- context --------------------------------
@@ -91,6 +92,7 @@ struct Ctx {
   size_t hv_scratch_bytes = 0;
   bool hv_dirty = true;
   const int64_t *cur_graph_row = nullptr;  // host row pointers of the graph being counted
+  DevGraph *cur_graph = nullptr;           // the graph being counted
   int heavy_degree = -1;         // sources of at least this degree take the heavy path (-1: tuned / default)
   int cur_tuned_heavy = -1;      // tuned threshold of the (graph, query) being enqueued, -1 none
   cudaStream_t own_stream = nullptr;  // created for graph capture when the caller's stream is the legacy one

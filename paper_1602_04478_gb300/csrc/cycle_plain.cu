@@ -106,6 +106,122 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uin
   }
 }
 
+// Pull form of the level build, for groups whose sources reach most of the
+// graph (the push form's atomics then collide on the same rows).  First the
+// level-1 bits (bit b of member[v] for v in N<(u_b), chi(v) != chi(u_b)),
+// then one warp per w below the group's highest source, lane b = source b:
+// the warp scans N(w) for level-1 vertices and each lane counts its own
+// source's by colour; the row is written where it is non-zero and the upper
+// half of member[w] (level-2 bits) is rewritten whole.  Rows whose bit is
+// clear are never read, so rows left from the previous group need no
+// clearing; the pass as a whole zeroes its scratch once it switches back to
+// the push form or ends.
+__global__ void k_pc_mark1(GraphView g, const uint8_t *colors, PcScratch S, PcGroup G) {
+  const int b = blockIdx.y;
+  const int32_t u = G.u[b];
+  const int cu = colors[u];
+  const int64_t ub = g.row[u];
+  const int du = g.lo_cnt[u];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < du; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = __ldg(g.col + ub + i);
+    if (colors[v] != cu) atomicOr(S.member + v, 1ull << b);
+  }
+}
+
+template <int L>
+__device__ __forceinline__ void pc_count(uint32_t (&cnt)[L], int c, uint32_t v) {
+  // c is the same in every lane of the warp: the branch does not diverge
+  switch (c) {
+    case 0: cnt[0] += v; break;
+    case 1: cnt[1] += v; break;
+    case 2: cnt[2] += v; break;
+    case 3: cnt[3] += v; break;
+    case 4: if (L > 4) cnt[L > 4 ? 4 : 0] += v; break;
+    default: if (L > 5) cnt[L > 5 ? 5 : 0] += v; break;
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kPcThreads) k_pc_levels_pull(GraphView g, const uint8_t *colors, PcScratch S,
+                                                               PcGroup G) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, b = lane;
+  const bool active = b < G.B;
+  const int32_t ub = active ? G.u[b] : -1;
+  const int cu = active ? colors[ub] : -1;
+  const int32_t umax = G.umax;
+  // member[v] as two 32-bit halves: [2v] level-1 bits (read here), [2v+1]
+  // level-2 bits (written here)
+  uint32_t *half = reinterpret_cast<uint32_t *>(S.member);
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t wi = warp0; wi < umax; wi += nwarps) {
+    const int32_t w = (int32_t)wi;
+    const int cw = colors[w];
+    const bool act = active && w < ub && cw != cu;
+    uint32_t cnt[L];
+#pragma unroll
+    for (int c = 0; c < L; c++) cnt[c] = 0;
+    if (__any_sync(FULL, act)) {
+      const int64_t wb = g.row[w];
+      const int deg = (int)(g.row[w + 1] - wb);
+      for (int base = 0; base < deg; base += 32) {
+        const int j = base + lane;
+        const int32_t vl = j < deg ? __ldg(g.col + wb + j) : INT32_MAX;
+        const bool past = __any_sync(FULL, vl >= umax);
+        uint32_t ml = vl < umax ? __ldcg(half + 2 * (int64_t)vl) : 0u;
+        const int cl = ml ? colors[vl] : cw;
+        if (cl == cw) ml = 0u;  // chi(v) = chi(w): no colourful path u-v-w
+        unsigned m = __ballot_sync(FULL, ml != 0u);
+        while (m) {
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const int t = m ? __ffs(m) - 1 : 0;
+            const bool valid = m != 0u;
+            m &= m - 1u;
+            const uint32_t mm = __shfl_sync(FULL, ml, t);
+            const int cc = __shfl_sync(FULL, cl, t);
+            if (valid) pc_count<L>(cnt, cc, (act && ((mm >> b) & 1u)) ? 1u : 0u);
+          }
+        }
+        if (past) break;
+      }
+    }
+    bool nz = false;
+#pragma unroll
+    for (int c = 0; c < L; c++) nz = nz || cnt[c] != 0u;
+    if (nz) {
+      uint32_t wd[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+      for (int c = 0; c < L; c++) wd[c >> 1] |= cnt[c] << (16 * (c & 1));
+      *(uint4 *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    }
+    const unsigned bits = __ballot_sync(FULL, nz);
+    if (lane == 0) half[2 * (int64_t)w + 1] = bits;
+  }
+}
+
+// Per rank u, the pairs the push form of the level build visits for u as a
+// source: v in N<(u), w in N(v) below u.
+__global__ void k_push_work(GraphView g, unsigned long long *out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = warp0; u < g.n; u += nwarps) {
+    const int64_t ub = g.row[u];
+    const int du = g.lo_cnt[u];
+    unsigned long long s = 0;
+    for (int i = lane; i < du; i += 32) {
+      const int32_t v = __ldg(g.col + ub + i);
+      const int64_t vb = g.row[v];
+      s += (unsigned long long)(lower_bound_i32(g.col, vb, g.row[v + 1], (int32_t)u) - vb);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[u] = s;
+  }
+}
+
 // ---------------------------------- pull ----------------------------------
 __host__ __device__ constexpr int pc_pair(int a, int b) {  // unordered colour pair, a != b
   return a > b ? a * (a - 1) / 2 + b : b * (b - 1) / 2 + a;
@@ -186,7 +302,8 @@ __global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const ui
       const int cl = wl < umax ? colors[wl] : cx;
       // chi(w) = chi(x) closes no colourful cycle
       const unsigned long long ml = cl != cx ? __ldg(S.member + wl) : 0ull;
-      unsigned m = __ballot_sync(FULL, ml != 0ull);
+      // C6 reads level-2 bits only (level-1 bits may be present from the pull-form build)
+      unsigned m = __ballot_sync(FULL, (L >= 6 ? (ml >> 32) : ml) != 0ull);
       while (m) {
         int32_t ww[4];
         int cc[4];
@@ -514,21 +631,79 @@ int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank) {
   return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }
 
+// Push-form work per source rank, computed once per graph (host copy).
+// Under stream capture it is not computed: the push form is then used.
+static int push_work(Ctx &c, const GraphView &g, const int64_t **out) {
+  *out = nullptr;
+  DevGraph *dg = c.cur_graph;
+  if (!dg) return CC_OK;
+  if (dg->h_push_work.empty()) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c.stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return CC_OK;
+    const size_t bytes = (size_t)g.n * 8;
+    u64 *d = (u64 *)dev_alloc(c, bytes);
+    if (!d) return CC_ERR_OOM;
+    k_push_work<<<152 * 8, 256, 0, c.stream>>>(g, d);
+    c.kernels++;
+    std::vector<int64_t> h((size_t)g.n);
+    const bool ok = cudaMemcpyAsync(h.data(), d, bytes, cudaMemcpyDeviceToHost, c.stream) == cudaSuccess &&
+                    cudaStreamSynchronize(c.stream) == cudaSuccess;
+    dev_free(c, d, bytes);
+    if (!ok) return CC_ERR_CUDA;
+    dg->h_push_work.swap(h);
+  }
+  *out = dg->h_push_work.data();
+  return CC_OK;
+}
+
+// A group takes the pull-form level build while its push work exceeds this
+// many times the edges of the rows below its highest source (the pull form
+// scans those rows once, without atomics).
+constexpr double kPullLevelsRatio = 0.5;
+
 template <int L>
 static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcScratch &S) {
   const int64_t n = a.g.n;
   const int sms = 152;
+  const int64_t *pw = nullptr;
+  if (L >= 5) {
+    int rc = push_work(c, a.g, &pw);
+    if (rc != CC_OK) return rc;
+  }
+  auto zero_levels = [&]() {
+    return cudaMemsetAsync(S.member, 0, (size_t)n * 8, c.stream) == cudaSuccess &&
+           cudaMemsetAsync(S.w2, 0, (size_t)kPcMaxB * n * 16, c.stream) == cudaSuccess;
+  };
+  bool pulled = false, pushed = false;
   for (int64_t top = n - 1; top >= first_rank; top -= kPcMaxB) {
     PcGroup G;
     G.B = (int)std::min<int64_t>(kPcMaxB, top - first_rank + 1);
     G.umax = (int32_t)top;
     for (int b = 0; b < G.B; b++) G.u[b] = (int32_t)(top - b);
     int64_t du = c.cur_graph_row[top + 1] - c.cur_graph_row[top];
-    dim3 gl((unsigned)std::max<int64_t>(1, std::min<int64_t>(sms * 2, (du * 32 + kPcThreads - 1) / kPcThreads)),
-            G.B);
-    timing_begin(c, "cycle_plain_levels");
-    k_pc_levels<L><<<gl, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G);
-    c.kernels++;
+    // the pull form serves a prefix of the groups (the highest sources)
+    bool use_pull = false;
+    if (pw && !pushed) {
+      double work = 0;
+      for (int b = 0; b < G.B; b++) work += (double)pw[G.u[b]];
+      use_pull = work > kPullLevelsRatio * (double)c.cur_graph_row[top];
+    }
+    if (!use_pull && pulled && !pushed && !zero_levels()) return CC_ERR_CUDA;
+    timing_begin(c, use_pull ? "cycle_plain_levels_pull" : "cycle_plain_levels");
+    if (use_pull) {
+      dim3 gm((unsigned)std::max<int64_t>(1, std::min<int64_t>(sms, (du + kPcThreads - 1) / kPcThreads)), G.B);
+      k_pc_mark1<<<gm, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G);
+      c.kernels++;
+      k_pc_levels_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G);
+      c.kernels++;
+      pulled = true;
+    } else {
+      dim3 gl((unsigned)std::max<int64_t>(1, std::min<int64_t>(sms * 2, (du * 32 + kPcThreads - 1) / kPcThreads)),
+              G.B);
+      k_pc_levels<L><<<gl, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G);
+      c.kernels++;
+      pushed = true;
+    }
     timing_end(c);
     timing_begin(c, "cycle_plain_pull");
     k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G, a.status);
@@ -539,6 +714,8 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
     k_pc_finish<<<1, 32, 0, c.stream>>>(S, G, a.multiplier, a.per_vertex, a.status);
     c.kernels++;
   }
+  // the scratch is all zero between launches
+  if (pulled && !pushed && !zero_levels()) return CC_ERR_CUDA;
   return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }
 

@@ -142,6 +142,35 @@ def test_triangle_sources_of_every_degree(cc, qname):
         cc.free_graph(gid)
 
 
+@pytest.mark.parametrize("qname", ["C5", "C6"])
+def test_both_level_build_forms(cc, qname):
+    # with every source heavy, the highest groups build their levels in the
+    # pull form and the rest in the push form; both feed the same closure
+    import paper_1602_04478_gb300 as P
+    k, e = QUERIES[qname]
+    g = graph("cl3000")
+    gid = cc.load_graph(g)
+    P.cc_set_heavy_degree(cc.h, 0)
+    try:
+        P.cc_set_coloring_seed(cc.h, 8)
+        qid = cc.set_query(k, e)
+        P.cc_set_timing(cc.h, True)
+        P.cc_reset_timing(cc.h)
+        pv, total = cc.count_per_vertex(gid, qid, 0)
+        names = P.cc_get_timing(cc.h)
+        P.cc_set_timing(cc.h, False)
+        assert "cycle_plain_levels_pull" in names and "cycle_plain_levels" in names, names
+        expect, _, per = O.dp_count(g, k, e, O.colors(8, 0, g.n, k), per_source=True)
+        assert total == expect
+        assert [int(x) for x in pv] == per
+        # and again, from the zero state the pass leaves behind
+        col, _, _ = cc.count(gid, qid, 0, 1)
+        assert int(col[0]) == expect
+    finally:
+        P.cc_set_heavy_degree(cc.h, -1)
+        cc.free_graph(gid)
+
+
 def test_scratch_reuse_across_graphs_and_queries(cc):
     # one context counts different graphs and cycle lengths in turn, every
     # source on the heavy path: scratch left by one (graph, query) must not
