@@ -256,20 +256,136 @@ __device__ __forceinline__ void pc_add_one(uint32_t (&A)[L], int c, uint32_t v) 
   for (int i = 0; i < L; i++) A[i] += (c == i) ? v : 0u;
 }
 
-// One warp per meeting vertex x (below the group's highest source), lane b =
-// source b.  x's neighbours are read 32 at a time: each lane loads one
-// neighbour, its colour and its membership word; the warp then visits the
-// neighbours that belong to any source's levels, four at a time (their
-// level-2 row loads in flight together), and each lane adds its own
-// source's row.  The visited neighbour's colour is the same in all lanes,
-// so a switch on it selects compile-time register indices without
-// divergence.  The closure at x reads the pair sums through shared memory
-// (the free colours depend on chi(u), which differs per lane).
+// One chunk of 32 neighbours of a meeting vertex x as one lane sees it:
+// the neighbour, its colour and its membership word (0 when it cannot
+// count: at or above the group's highest source, or coloured chi(x)).
+struct PcChunk {
+  int32_t w;
+  int c;
+  unsigned long long m;
+};
+
+__device__ __forceinline__ PcChunk pc_load_chunk(const GraphView &g, const uint8_t *colors, const PcScratch &S,
+                                                 int64_t xb, int deg, int j, int cx, int32_t umax) {
+  PcChunk k;
+  k.w = j < deg ? __ldg(g.col + xb + j) : INT32_MAX;
+  k.c = k.w < umax ? colors[k.w] : cx;
+  k.m = k.c != cx ? __ldg(S.member + k.w) : 0ull;
+  return k;
+}
+
+// Visit the members among one chunk: four at a time (their level-2 row
+// loads in flight together); each lane adds its own source's row.  The
+// visited neighbour's colour is the same in all lanes, so a switch on it
+// selects compile-time register indices without divergence.
 template <int L>
-__global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const uint8_t *colors, PcScratch S,
-                                                        PcGroup G, u64 *status) {
+__device__ __forceinline__ void pc_visit_chunk(const PcScratch &S, const PcChunk &k, int b, bool act, int32_t ub,
+                                               int cu, uint32_t (&A)[L], uint32_t (&P)[L * (L - 1) / 2],
+                                               bool &hit) {
+  constexpr unsigned FULL = 0xffffffffu;
+  // C6 reads level-2 bits only (level-1 bits may be present from the pull-form build)
+  unsigned m = __ballot_sync(FULL, (L >= 6 ? (k.m >> 32) : k.m) != 0ull);
+  while (m) {
+    int32_t ww[4];
+    int cc[4];
+    unsigned long long mm[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int t = m ? __ffs(m) - 1 : 0;
+      const bool valid = m != 0u;
+      m &= m - 1u;
+      ww[q] = __shfl_sync(FULL, k.w, t);
+      cc[q] = valid ? __shfl_sync(FULL, k.c, t) : -1;
+      const unsigned long long mt = __shfl_sync(FULL, k.m, t);
+      mm[q] = valid ? mt : 0ull;
+    }
+    uint4 rr[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const bool in = act && ww[q] < ub && cc[q] != cu;
+      if (L <= 5 && in && ((mm[q] >> b) & 1ull)) {
+        pc_add_one<L>(A, cc[q], 1u);
+        hit = true;
+      }
+      rr[q] = make_uint4(0, 0, 0, 0);
+      if (L >= 5 && in && ((mm[q] >> (32 + b)) & 1ull)) {
+        rr[q] = __ldg((const uint4 *)(S.w2 + ((int64_t)ww[q] * kPcMaxB + b) * 8));
+        hit = true;
+      }
+    }
+    if (L >= 5) {
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (cc[q] >= 0) pc_add_row_dyn<L>(P, rr[q], cc[q]);
+    }
+  }
+}
+
+// All chunks of one meeting vertex (the first one already loaded) and the
+// closure at it, added to tot.  The closure reads the pair sums through
+// shared memory: the free colours depend on chi(u), which differs per lane.
+template <int L>
+__device__ __forceinline__ void pc_meet(const GraphView &g, const uint8_t *colors, const PcScratch &S, int32_t x,
+                                        int cx, int64_t xb, int deg, PcChunk k, int lane, bool active, int32_t ub,
+                                        int cu, int32_t umax, uint32_t (*sA)[kPcThreads],
+                                        uint32_t (*sP)[kPcThreads], int tid, u64 &tot, unsigned &ovf) {
   constexpr int NP = L * (L - 1) / 2;
   constexpr unsigned FULL = 0xffffffffu;
+  const bool act = active && x < ub && cx != cu;
+  if (!__any_sync(FULL, act)) return;
+  uint32_t A[L], P[NP];
+#pragma unroll
+  for (int c = 0; c < L; c++) A[c] = 0;
+#pragma unroll
+  for (int j = 0; j < NP; j++) P[j] = 0;
+  bool hit = false;
+  for (int base = 0;;) {
+    // the row is rank ordered: past the highest source, nothing further counts
+    const bool past = __any_sync(FULL, k.w >= umax);
+    pc_visit_chunk<L>(S, k, lane, act, ub, cu, A, P, hit);
+    base += 32;
+    if (past || base >= deg) break;
+    k = pc_load_chunk(g, colors, S, xb, deg, base + lane, cx, umax);
+  }
+  if (!act || !hit) return;
+  // free colours f0 < f1 < ... (all but chi(u) and chi(x))
+  uint32_t rest = ((1u << L) - 1u) & ~((1u << cu) | (1u << cx));
+  int f[4];
+#pragma unroll
+  for (int i = 0; i < L - 2; i++) {
+    f[i] = __ffs(rest) - 1;
+    rest &= rest - 1u;
+  }
+  if (L <= 5) {
+#pragma unroll
+    for (int c = 0; c < L; c++) sA[c][tid] = A[c];
+  }
+  if (L >= 5) {
+#pragma unroll
+    for (int j = 0; j < NP; j++) sP[j][tid] = P[j];
+  }
+  if (L == 4) {
+    tot = add_ck(tot, mul_ck(2ull, mul_ck(sA[f[0]][tid], sA[f[1]][tid], ovf), ovf), ovf);
+  } else if (L == 5) {
+    u64 t = mul_ck(sA[f[0]][tid], sP[pc_pair(f[1], f[2])][tid], ovf);
+    t = add_ck(t, mul_ck(sA[f[1]][tid], sP[pc_pair(f[0], f[2])][tid], ovf), ovf);
+    t = add_ck(t, mul_ck(sA[f[2]][tid], sP[pc_pair(f[0], f[1])][tid], ovf), ovf);
+    tot = add_ck(tot, t, ovf);
+  } else {
+    u64 t = (u64)sP[pc_pair(f[0], f[1])][tid] * sP[pc_pair(f[2], f[3])][tid];
+    t = add_ck(t, (u64)sP[pc_pair(f[0], f[2])][tid] * sP[pc_pair(f[1], f[3])][tid], ovf);
+    t = add_ck(t, (u64)sP[pc_pair(f[0], f[3])][tid] * sP[pc_pair(f[1], f[2])][tid], ovf);
+    tot = add_ck(tot, mul_ck(2ull, t, ovf), ovf);
+  }
+}
+
+// One warp per pair of meeting vertices (x, x + 1) below the group's highest
+// source, lane b = source b.  The first chunks of both are loaded together
+// (two dependent load chains in flight), then each is visited and closed.
+template <int L>
+__global__ void __launch_bounds__(kPcThreads, 3) k_pc_pull(GraphView g, const uint8_t *colors, PcScratch S,
+                                                        PcGroup G, u64 *status) {
+  constexpr int NP = L * (L - 1) / 2;
   __shared__ uint32_t sP[L >= 5 ? NP : 1][kPcThreads];
   __shared__ uint32_t sA[L <= 5 ? L : 1][kPcThreads];
   const int tid = threadIdx.x, lane = tid & 31, b = lane;
@@ -281,95 +397,17 @@ __global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const ui
   unsigned ovf = 0;
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t xi = warp0; xi < umax; xi += nwarps) {
-    const int32_t x = (int32_t)xi;
-    const int cx = colors[x];
-    const bool act = active && x < ub && cx != cu;
-    if (!__any_sync(FULL, act)) continue;
-    const int64_t xb = g.row[x];
-    const int deg = (int)(g.row[x + 1] - xb);
-    uint32_t A[L], P[NP];
-#pragma unroll
-    for (int c = 0; c < L; c++) A[c] = 0;
-#pragma unroll
-    for (int j = 0; j < NP; j++) P[j] = 0;
-    bool hit = false;
-    for (int base = 0; base < deg; base += 32) {
-      const int j = base + lane;
-      const int32_t wl = j < deg ? __ldg(g.col + xb + j) : INT32_MAX;
-      // the row is rank ordered: past the highest source, nothing further counts
-      const bool past = __any_sync(FULL, wl >= umax);
-      const int cl = wl < umax ? colors[wl] : cx;
-      // chi(w) = chi(x) closes no colourful cycle
-      const unsigned long long ml = cl != cx ? __ldg(S.member + wl) : 0ull;
-      // C6 reads level-2 bits only (level-1 bits may be present from the pull-form build)
-      unsigned m = __ballot_sync(FULL, (L >= 6 ? (ml >> 32) : ml) != 0ull);
-      while (m) {
-        int32_t ww[4];
-        int cc[4];
-        unsigned long long mm[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int t = m ? __ffs(m) - 1 : 0;
-          const bool valid = m != 0u;
-          m &= m - 1u;
-          ww[q] = __shfl_sync(FULL, wl, t);
-          cc[q] = valid ? __shfl_sync(FULL, cl, t) : -1;
-          const unsigned long long mt = __shfl_sync(FULL, ml, t);
-          mm[q] = valid ? mt : 0ull;
-        }
-        uint4 rr[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const bool in = act && ww[q] < ub && cc[q] != cu;
-          if (L <= 5 && in && ((mm[q] >> b) & 1ull)) {
-            pc_add_one<L>(A, cc[q], 1u);
-            hit = true;
-          }
-          rr[q] = make_uint4(0, 0, 0, 0);
-          if (L >= 5 && in && ((mm[q] >> (32 + b)) & 1ull)) {
-            rr[q] = __ldg((const uint4 *)(S.w2 + ((int64_t)ww[q] * kPcMaxB + b) * 8));
-            hit = true;
-          }
-        }
-        if (L >= 5) {
-#pragma unroll
-          for (int q = 0; q < 4; q++)
-            if (cc[q] >= 0) pc_add_row_dyn<L>(P, rr[q], cc[q]);
-        }
-      }
-      if (past) break;
-    }
-    if (!act || !hit) continue;
-    // free colours f0 < f1 < ... (all but chi(u) and chi(x))
-    uint32_t rest = ((1u << L) - 1u) & ~((1u << cu) | (1u << cx));
-    int f[4];
-#pragma unroll
-    for (int i = 0; i < L - 2; i++) {
-      f[i] = __ffs(rest) - 1;
-      rest &= rest - 1u;
-    }
-    if (L <= 5) {
-#pragma unroll
-      for (int c = 0; c < L; c++) sA[c][tid] = A[c];
-    }
-    if (L >= 5) {
-#pragma unroll
-      for (int j = 0; j < NP; j++) sP[j][tid] = P[j];
-    }
-    if (L == 4) {
-      tot = add_ck(tot, mul_ck(2ull, mul_ck(sA[f[0]][tid], sA[f[1]][tid], ovf), ovf), ovf);
-    } else if (L == 5) {
-      u64 t = mul_ck(sA[f[0]][tid], sP[pc_pair(f[1], f[2])][tid], ovf);
-      t = add_ck(t, mul_ck(sA[f[1]][tid], sP[pc_pair(f[0], f[2])][tid], ovf), ovf);
-      t = add_ck(t, mul_ck(sA[f[2]][tid], sP[pc_pair(f[0], f[1])][tid], ovf), ovf);
-      tot = add_ck(tot, t, ovf);
-    } else {
-      u64 t = (u64)sP[pc_pair(f[0], f[1])][tid] * sP[pc_pair(f[2], f[3])][tid];
-      t = add_ck(t, (u64)sP[pc_pair(f[0], f[2])][tid] * sP[pc_pair(f[1], f[3])][tid], ovf);
-      t = add_ck(t, (u64)sP[pc_pair(f[0], f[3])][tid] * sP[pc_pair(f[1], f[2])][tid], ovf);
-      tot = add_ck(tot, mul_ck(2ull, t, ovf), ovf);
-    }
+  for (int64_t xi = 2 * warp0; xi < umax; xi += 2 * nwarps) {
+    const int32_t x0 = (int32_t)xi;
+    const bool two = xi + 1 < umax;
+    const int32_t x1 = two ? x0 + 1 : x0;
+    const int cx0 = colors[x0], cx1 = colors[x1];
+    const int64_t xb0 = g.row[x0], xb1 = g.row[x1], xe1 = g.row[x1 + 1];
+    const int deg0 = (int)(xb1 - xb0), deg1 = two ? (int)(xe1 - xb1) : 0;
+    const PcChunk k0 = pc_load_chunk(g, colors, S, xb0, deg0, lane, cx0, umax);
+    const PcChunk k1 = pc_load_chunk(g, colors, S, xb1, deg1, lane, cx1, umax);
+    pc_meet<L>(g, colors, S, x0, cx0, xb0, deg0, k0, lane, active, ub, cu, umax, sA, sP, tid, tot, ovf);
+    if (two) pc_meet<L>(g, colors, S, x1, cx1, xb1, deg1, k1, lane, active, ub, cu, umax, sA, sP, tid, tot, ovf);
   }
   if (active && tot) atomic_add_ck(S.totals + b, tot, ovf);
   flag_overflow(status, ovf);
@@ -659,7 +697,7 @@ static int push_work(Ctx &c, const GraphView &g, const int64_t **out) {
 // A group takes the pull-form level build while its push work exceeds this
 // many times the edges of the rows below its highest source (the pull form
 // scans those rows once, without atomics).
-constexpr double kPullLevelsRatio = 0.5;
+constexpr double kPullLevelsRatio = 1.0;
 
 template <int L>
 static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcScratch &S) {
@@ -706,7 +744,7 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
     }
     timing_end(c);
     timing_begin(c, "cycle_plain_pull");
-    k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G, a.status);
+    k_pc_pull<L><<<sms * 3, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G, a.status);
     c.kernels++;
     timing_end(c);
     k_pc_clear<L><<<sms, 256, 0, c.stream>>>(a.g, a.colors, S, G);
