@@ -400,10 +400,10 @@ __global__ void __launch_bounds__(kPcThreads, 3) k_pc_pull(GraphView g, const ui
   for (int64_t xi = 2 * warp0; xi < umax; xi += 2 * nwarps) {
     const int32_t x0 = (int32_t)xi;
     const bool two = xi + 1 < umax;
-    const int32_t x1 = two ? x0 + 1 : x0;
-    const int cx0 = colors[x0], cx1 = colors[x1];
-    const int64_t xb0 = g.row[x0], xb1 = g.row[x1], xe1 = g.row[x1 + 1];
-    const int deg0 = (int)(xb1 - xb0), deg1 = two ? (int)(xe1 - xb1) : 0;
+    const int32_t x1 = x0 + 1;  // a vertex only when `two` (x1 <= umax < n either way)
+    const int cx0 = colors[x0], cx1 = two ? colors[x1] : 0;
+    const int64_t xb0 = g.row[x0], xb1 = g.row[x1], xe1 = two ? g.row[x1 + 1] : xb1;
+    const int deg0 = (int)(xb1 - xb0), deg1 = (int)(xe1 - xb1);
     const PcChunk k0 = pc_load_chunk(g, colors, S, xb0, deg0, lane, cx0, umax);
     const PcChunk k1 = pc_load_chunk(g, colors, S, xb1, deg1, lane, cx1, umax);
     pc_meet<L>(g, colors, S, x0, cx0, xb0, deg0, k0, lane, active, ub, cu, umax, sA, sP, tid, tot, ovf);
