@@ -72,6 +72,17 @@ int ensure_hv_scratch(Ctx &c, size_t bytes) {
   return CC_OK;
 }
 
+int ensure_tag_scratch(Ctx &c, size_t bytes) {
+  if (c.tag_scratch_bytes >= bytes) return CC_OK;
+  if (c.tag_scratch) {
+    cudaStreamSynchronize(c.stream);
+    dev_free(c, c.tag_scratch, c.tag_scratch_bytes);
+  }
+  c.tag_scratch = dev_alloc(c, bytes);
+  c.tag_scratch_bytes = c.tag_scratch ? bytes : 0;
+  return c.tag_scratch ? CC_OK : CC_ERR_OOM;
+}
+
 void timing_begin(Ctx &c, const char *name) {
   if (!c.timing) return;
   cudaEvent_t a, b;
@@ -383,6 +394,7 @@ void cc_destroy(cc_ctx *ctx) {
   for (auto &g : c.graphs) graph_free(c, g.second);
   dev_free(c, c.scratch, c.scratch_bytes);
   dev_free(c, c.hv_scratch, c.hv_scratch_bytes);
+  dev_free(c, c.tag_scratch, c.tag_scratch_bytes);
   batch_cache_clear(c);
   dev_free(c, c.lut_rank, 4096 * 2);
   dev_free(c, c.lut_unrank, 13 * kUnrankStride * 2);

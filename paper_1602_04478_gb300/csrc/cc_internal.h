@@ -90,6 +90,8 @@ struct Ctx {
   unsigned epoch = 0;
   void *hv_scratch = nullptr;    // heavy-source cycle scratch (all zero between launches)
   size_t hv_scratch_bytes = 0;
+  void *tag_scratch = nullptr;   // colour-tagged adjacency, rewritten every pass (no zero invariant)
+  size_t tag_scratch_bytes = 0;
   bool hv_dirty = true;
   const int64_t *cur_graph_row = nullptr;  // host row pointers of the graph being counted
   DevGraph *cur_graph = nullptr;           // the graph being counted
@@ -110,6 +112,7 @@ void *dev_alloc(Ctx &c, size_t bytes);
 void dev_free(Ctx &c, void *p, size_t bytes);
 int ensure_scratch(Ctx &c, size_t bytes);
 int ensure_hv_scratch(Ctx &c, size_t bytes);  // grows and, when fresh or dirty, zeroes the heavy scratch
+int ensure_tag_scratch(Ctx &c, size_t bytes); // grows only
 
 // kernel-launch bracketing for the optional timing
 void batch_cache_clear(Ctx &c);  // drop captured batch graphs and their buffers

@@ -567,7 +567,9 @@ int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   }
   a.light_end = (int32_t)lo;
   // plain C4..C6: 16-bit level-2 rows on the heavy path need max degree < 2^16
-  const bool plain = plain_cycle_eligible(a) && !a.count_units && (c.cur_graph_row[n] - c.cur_graph_row[n - 1]) < 65536;
+  // the plain kernels keep 16-bit row entries (degree < 2^16) and tag neighbours with their colour (n < 2^29)
+  const bool plain = plain_cycle_eligible(a) && !a.count_units && (c.cur_graph_row[n] - c.cur_graph_row[n - 1]) < 65536 &&
+                     n < ((int64_t)1 << 29);
   if (a.light_end < n) {
     int rc = plain ? run_plain_heavy(c, a, a.light_end) : run_heavy(c, a, a.light_end, heavy_group_size(a));
     if (rc != CC_OK) return rc;

@@ -34,9 +34,14 @@ namespace cc {
 constexpr int kPcMaxB = 32;  // sources per heavy group (one lane each)
 constexpr int kPcThreads = 256;
 
+// colour-tagged adjacency: entry = neighbour | colour << kTagShift (n < 2^29, k <= 8)
+constexpr int kTagShift = 29;
+constexpr uint32_t kTagMask = (1u << kTagShift) - 1u;
+
 struct PcScratch {
   uint16_t *w2;                // [n][32 sources][8 colours] level-2 rows (u16: max degree < 65536)
   unsigned long long *member;  // [n]: bit b level 1 of source b, bit 32+b level 2 (b < 32)
+  uint32_t *anym;              // [(n + 31) / 32]: bit w set when w is in some level the pull reads
   int32_t *list;               // [B][n] level-2 vertices (for clearing)
   int *cnt;                    // [B]
   u64 *totals;                 // [B]
@@ -71,7 +76,10 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uin
     const int32_t v = __ldg(g.col + ub + i);
     const int cv = colors[v];
     if (cv == cu) continue;
-    if (L <= 5 && lane == 0) atomicOr(S.member + v, 1ull << b);
+    if (L <= 5 && lane == 0) {
+      atomicOr(S.member + v, 1ull << b);
+      atomicOr(S.anym + (v >> 5), 1u << (v & 31));
+    }
     if (L == 4) continue;
     const int64_t vb = g.row[v], vend = g.row[v + 1];
     for (int64_t e0 = vb; e0 < vend; e0 += 32) {
@@ -90,6 +98,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uin
           if (!((__ldcg(S.member + w) >> (32 + b)) & 1ull)) {
             const unsigned long long old = atomicOr(S.member + w, 1ull << (32 + b));
             need = !((old >> (32 + b)) & 1ull);
+            if (need) atomicOr(S.anym + (w >> 5), 1u << (w & 31));
           }
         }
       }
@@ -116,7 +125,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uin
 // clear are never read, so rows left from the previous group need no
 // clearing; the pass as a whole zeroes its scratch once it switches back to
 // the push form or ends.
-__global__ void k_pc_mark1(GraphView g, const uint8_t *colors, PcScratch S, PcGroup G) {
+__global__ void k_pc_mark1(GraphView g, const uint8_t *colors, PcScratch S, PcGroup G, bool level1_read) {
   const int b = blockIdx.y;
   const int32_t u = G.u[b];
   const int cu = colors[u];
@@ -124,7 +133,10 @@ __global__ void k_pc_mark1(GraphView g, const uint8_t *colors, PcScratch S, PcGr
   const int du = g.lo_cnt[u];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < du; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = __ldg(g.col + ub + i);
-    if (colors[v] != cu) atomicOr(S.member + v, 1ull << b);
+    if (colors[v] != cu) {
+      atomicOr(S.member + v, 1ull << b);
+      if (level1_read) atomicOr(S.anym + (v >> 5), 1u << (v & 31));
+    }
   }
 }
 
@@ -197,7 +209,18 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels_pull(GraphView g, cons
       *(uint4 *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
     }
     const unsigned bits = __ballot_sync(FULL, nz);
-    if (lane == 0) half[2 * (int64_t)w + 1] = bits;
+    if (lane == 0) {
+      half[2 * (int64_t)w + 1] = bits;
+      if (bits) atomicOr(S.anym + (w >> 5), 1u << (w & 31));
+    }
+  }
+}
+
+// The colour-tagged adjacency of one colouring: tag[e] = col[e] | chi(col[e]) << kTagShift.
+__global__ void k_tag_cols(GraphView g, const uint8_t *colors, uint32_t *tag) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g.nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t w = __ldg(g.col + e);
+    tag[e] = (uint32_t)w | ((uint32_t)colors[w] << kTagShift);
   }
 }
 
@@ -258,19 +281,24 @@ __device__ __forceinline__ void pc_add_one(uint32_t (&A)[L], int c, uint32_t v) 
 
 // One chunk of 32 neighbours of a meeting vertex x as one lane sees it:
 // the neighbour, its colour and its membership word (0 when it cannot
-// count: at or above the group's highest source, or coloured chi(x)).
+// count: at or above the group's highest source, coloured chi(x), or in no
+// source's levels).  The colour comes with the neighbour from the tagged
+// adjacency; the membership word is read only where the group's one-bit map
+// says the neighbour belongs to some level.
 struct PcChunk {
   int32_t w;
   int c;
   unsigned long long m;
 };
 
-__device__ __forceinline__ PcChunk pc_load_chunk(const GraphView &g, const uint8_t *colors, const PcScratch &S,
-                                                 int64_t xb, int deg, int j, int cx, int32_t umax) {
+__device__ __forceinline__ PcChunk pc_load_chunk(const uint32_t *tag, const PcScratch &S, int64_t xb, int deg, int j,
+                                                 int cx, int32_t umax) {
   PcChunk k;
-  k.w = j < deg ? __ldg(g.col + xb + j) : INT32_MAX;
-  k.c = k.w < umax ? colors[k.w] : cx;
-  k.m = k.c != cx ? __ldg(S.member + k.w) : 0ull;
+  const uint32_t t = j < deg ? __ldg(tag + xb + j) : 0xFFFFFFFFu;
+  k.w = j < deg ? (int32_t)(t & kTagMask) : INT32_MAX;
+  k.c = k.w < umax ? (int)(t >> kTagShift) : cx;
+  const bool any = k.c != cx && ((__ldg(S.anym + (k.w >> 5)) >> (k.w & 31)) & 1u);
+  k.m = any ? __ldg(S.member + k.w) : 0ull;
   return k;
 }
 
@@ -325,7 +353,7 @@ __device__ __forceinline__ void pc_visit_chunk(const PcScratch &S, const PcChunk
 // closure at it, added to tot.  The closure reads the pair sums through
 // shared memory: the free colours depend on chi(u), which differs per lane.
 template <int L>
-__device__ __forceinline__ void pc_meet(const GraphView &g, const uint8_t *colors, const PcScratch &S, int32_t x,
+__device__ __forceinline__ void pc_meet(const uint32_t *tag, const PcScratch &S, int32_t x,
                                         int cx, int64_t xb, int deg, PcChunk k, int lane, bool active, int32_t ub,
                                         int cu, int32_t umax, uint32_t (*sA)[kPcThreads],
                                         uint32_t (*sP)[kPcThreads], int tid, u64 &tot, unsigned &ovf) {
@@ -345,7 +373,7 @@ __device__ __forceinline__ void pc_meet(const GraphView &g, const uint8_t *color
     pc_visit_chunk<L>(S, k, lane, act, ub, cu, A, P, hit);
     base += 32;
     if (past || base >= deg) break;
-    k = pc_load_chunk(g, colors, S, xb, deg, base + lane, cx, umax);
+    k = pc_load_chunk(tag, S, xb, deg, base + lane, cx, umax);
   }
   if (!act || !hit) return;
   // free colours f0 < f1 < ... (all but chi(u) and chi(x))
@@ -379,12 +407,11 @@ __device__ __forceinline__ void pc_meet(const GraphView &g, const uint8_t *color
   }
 }
 
-// One warp per pair of meeting vertices (x, x + 1) below the group's highest
-// source, lane b = source b.  The first chunks of both are loaded together
-// (two dependent load chains in flight), then each is visited and closed.
+// One warp per meeting vertex x below the group's highest source, lane b =
+// source b.
 template <int L>
-__global__ void __launch_bounds__(kPcThreads, 3) k_pc_pull(GraphView g, const uint8_t *colors, PcScratch S,
-                                                        PcGroup G, u64 *status) {
+__global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const uint32_t *tag, PcScratch S, PcGroup G,
+                                                        const uint8_t *colors, u64 *status) {
   constexpr int NP = L * (L - 1) / 2;
   __shared__ uint32_t sP[L >= 5 ? NP : 1][kPcThreads];
   __shared__ uint32_t sA[L <= 5 ? L : 1][kPcThreads];
@@ -397,17 +424,13 @@ __global__ void __launch_bounds__(kPcThreads, 3) k_pc_pull(GraphView g, const ui
   unsigned ovf = 0;
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t xi = 2 * warp0; xi < umax; xi += 2 * nwarps) {
-    const int32_t x0 = (int32_t)xi;
-    const bool two = xi + 1 < umax;
-    const int32_t x1 = x0 + 1;  // a vertex only when `two` (x1 <= umax < n either way)
-    const int cx0 = colors[x0], cx1 = two ? colors[x1] : 0;
-    const int64_t xb0 = g.row[x0], xb1 = g.row[x1], xe1 = two ? g.row[x1 + 1] : xb1;
-    const int deg0 = (int)(xb1 - xb0), deg1 = (int)(xe1 - xb1);
-    const PcChunk k0 = pc_load_chunk(g, colors, S, xb0, deg0, lane, cx0, umax);
-    const PcChunk k1 = pc_load_chunk(g, colors, S, xb1, deg1, lane, cx1, umax);
-    pc_meet<L>(g, colors, S, x0, cx0, xb0, deg0, k0, lane, active, ub, cu, umax, sA, sP, tid, tot, ovf);
-    if (two) pc_meet<L>(g, colors, S, x1, cx1, xb1, deg1, k1, lane, active, ub, cu, umax, sA, sP, tid, tot, ovf);
+  for (int64_t xi = warp0; xi < umax; xi += nwarps) {
+    const int32_t x = (int32_t)xi;
+    const int cx = colors[x];
+    const int64_t xb = g.row[x];
+    const int deg = (int)(g.row[x + 1] - xb);
+    const PcChunk k = pc_load_chunk(tag, S, xb, deg, lane, cx, umax);
+    pc_meet<L>(tag, S, x, cx, xb, deg, k, lane, active, ub, cu, umax, sA, sP, tid, tot, ovf);
   }
   if (active && tot) atomic_add_ck(S.totals + b, tot, ovf);
   flag_overflow(status, ovf);
@@ -697,10 +720,10 @@ static int push_work(Ctx &c, const GraphView &g, const int64_t **out) {
 // A group takes the pull-form level build while its push work exceeds this
 // many times the edges of the rows below its highest source (the pull form
 // scans those rows once, without atomics).
-constexpr double kPullLevelsRatio = 1.0;
+constexpr double kPullLevelsRatio = 0.7;
 
 template <int L>
-static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcScratch &S) {
+static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcScratch &S, const uint32_t *tag) {
   const int64_t n = a.g.n;
   const int sms = 152;
   const int64_t *pw = nullptr;
@@ -712,6 +735,9 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
     return cudaMemsetAsync(S.member, 0, (size_t)n * 8, c.stream) == cudaSuccess &&
            cudaMemsetAsync(S.w2, 0, (size_t)kPcMaxB * n * 16, c.stream) == cudaSuccess;
   };
+  const size_t anym_bytes = (size_t)((n + 31) / 32) * 4;
+  k_tag_cols<<<sms * 8, 256, 0, c.stream>>>(a.g, a.colors, (uint32_t *)tag);
+  c.kernels++;
   bool pulled = false, pushed = false;
   for (int64_t top = n - 1; top >= first_rank; top -= kPcMaxB) {
     PcGroup G;
@@ -727,10 +753,12 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
       use_pull = work > kPullLevelsRatio * (double)c.cur_graph_row[top];
     }
     if (!use_pull && pulled && !pushed && !zero_levels()) return CC_ERR_CUDA;
+    // the one-bit member map is rebuilt for every group
+    if (cudaMemsetAsync(S.anym, 0, anym_bytes, c.stream) != cudaSuccess) return CC_ERR_CUDA;
     timing_begin(c, use_pull ? "cycle_plain_levels_pull" : "cycle_plain_levels");
     if (use_pull) {
       dim3 gm((unsigned)std::max<int64_t>(1, std::min<int64_t>(sms, (du + kPcThreads - 1) / kPcThreads)), G.B);
-      k_pc_mark1<<<gm, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G);
+      k_pc_mark1<<<gm, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G, L <= 5);
       c.kernels++;
       k_pc_levels_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G);
       c.kernels++;
@@ -744,7 +772,7 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
     }
     timing_end(c);
     timing_begin(c, "cycle_plain_pull");
-    k_pc_pull<L><<<sms * 3, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G, a.status);
+    k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S, G, a.colors, a.status);
     c.kernels++;
     timing_end(c);
     k_pc_clear<L><<<sms, 256, 0, c.stream>>>(a.g, a.colors, S, G);
@@ -754,6 +782,7 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
   }
   // the scratch is all zero between launches
   if (pulled && !pushed && !zero_levels()) return CC_ERR_CUDA;
+  if (cudaMemsetAsync(S.anym, 0, anym_bytes, c.stream) != cudaSuccess) return CC_ERR_CUDA;
   return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }
 
@@ -779,6 +808,7 @@ int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank) {
   size_t o_list = lv2 ? take((size_t)kPcMaxB * n * 4) : 0;
   size_t o_cnt = take(kPcMaxB * 4);
   size_t o_tot = take(kPcMaxB * 8);
+  size_t o_anym = take((size_t)((n + 31) / 32) * 4);
   size_t need = off;
   int rc0 = ensure_hv_scratch(c, need);
   if (rc0 != CC_OK) return rc0;
@@ -789,9 +819,14 @@ int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank) {
   S.list = (int32_t *)(base + o_list);
   S.cnt = (int *)(base + o_cnt);
   S.totals = (u64 *)(base + o_tot);
-  if (a.L == 4) return run_plain_L<4>(c, a, first_rank, S);
-  if (a.L == 5) return run_plain_L<5>(c, a, first_rank, S);
-  return run_plain_L<6>(c, a, first_rank, S);
+  S.anym = (uint32_t *)(base + o_anym);
+  // the tagged adjacency is rewritten every pass: it lives outside the
+  // heavy scratch, whose contents are zero between launches
+  if ((rc0 = ensure_tag_scratch(c, (size_t)std::max<int64_t>(a.g.nnz, 1) * 4)) != CC_OK) return rc0;
+  const uint32_t *tag = (const uint32_t *)c.tag_scratch;
+  if (a.L == 4) return run_plain_L<4>(c, a, first_rank, S, tag);
+  if (a.L == 5) return run_plain_L<5>(c, a, first_rank, S, tag);
+  return run_plain_L<6>(c, a, first_rank, S, tag);
 }
 
 }  // namespace cc
