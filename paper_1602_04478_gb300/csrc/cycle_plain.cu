@@ -302,50 +302,68 @@ __device__ __forceinline__ PcChunk pc_load_chunk(const uint32_t *tag, const PcSc
   return k;
 }
 
-// Visit the members among one chunk: four at a time (their level-2 row
-// loads in flight together); each lane adds its own source's row.  The
-// visited neighbour's colour is the same in all lanes, so a switch on it
-// selects compile-time register indices without divergence.
+// Member lanes of a chunk.  C6 reads level-2 bits only (level-1 bits may be
+// present from the pull-form build).
 template <int L>
-__device__ __forceinline__ void pc_visit_chunk(const PcScratch &S, const PcChunk &k, int b, bool act, int32_t ub,
-                                               int cu, uint32_t (&A)[L], uint32_t (&P)[L * (L - 1) / 2],
-                                               bool &hit) {
+__device__ __forceinline__ unsigned pc_members(const PcChunk &k) {
+  return __ballot_sync(0xffffffffu, (L >= 6 ? (k.m >> 32) : k.m) != 0ull);
+}
+
+// One visited neighbour w (colour c, membership word mm) as lane b sees it.
+template <int L>
+__device__ __forceinline__ uint4 pc_take(const PcScratch &S, int32_t w, int c, unsigned long long mm, int b,
+                                         bool act, int32_t ub, int cu, uint32_t (&A)[L], bool &hit) {
+  const bool in = act && w < ub && c != cu;
+  if (L <= 5 && in && ((mm >> b) & 1ull)) {
+    pc_add_one<L>(A, c, 1u);
+    hit = true;
+  }
+  uint4 r = make_uint4(0, 0, 0, 0);
+  if (L >= 5 && in && ((mm >> (32 + b)) & 1ull)) {
+    r = __ldg((const uint4 *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8));
+    hit = true;
+  }
+  return r;
+}
+
+// Visit the members of one chunk (mask m): four at a time while at least
+// four remain (their level-2 row loads in flight together), then one at a
+// time; each lane adds its own source's row.  The visited neighbour's colour
+// is the same in all lanes, so a switch on it selects compile-time register
+// indices without divergence.
+template <int L>
+__device__ __forceinline__ void pc_visit_chunk(const PcScratch &S, const PcChunk &k, unsigned m, int b, bool act,
+                                               int32_t ub, int cu, uint32_t (&A)[L],
+                                               uint32_t (&P)[L * (L - 1) / 2], bool &hit) {
   constexpr unsigned FULL = 0xffffffffu;
-  // C6 reads level-2 bits only (level-1 bits may be present from the pull-form build)
-  unsigned m = __ballot_sync(FULL, (L >= 6 ? (k.m >> 32) : k.m) != 0ull);
-  while (m) {
+  while (__popc(m) >= 4) {
     int32_t ww[4];
     int cc[4];
     unsigned long long mm[4];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-      const int t = m ? __ffs(m) - 1 : 0;
-      const bool valid = m != 0u;
+      const int t = __ffs(m) - 1;
       m &= m - 1u;
       ww[q] = __shfl_sync(FULL, k.w, t);
-      cc[q] = valid ? __shfl_sync(FULL, k.c, t) : -1;
-      const unsigned long long mt = __shfl_sync(FULL, k.m, t);
-      mm[q] = valid ? mt : 0ull;
+      cc[q] = __shfl_sync(FULL, k.c, t);
+      mm[q] = __shfl_sync(FULL, k.m, t);
     }
     uint4 rr[4];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const bool in = act && ww[q] < ub && cc[q] != cu;
-      if (L <= 5 && in && ((mm[q] >> b) & 1ull)) {
-        pc_add_one<L>(A, cc[q], 1u);
-        hit = true;
-      }
-      rr[q] = make_uint4(0, 0, 0, 0);
-      if (L >= 5 && in && ((mm[q] >> (32 + b)) & 1ull)) {
-        rr[q] = __ldg((const uint4 *)(S.w2 + ((int64_t)ww[q] * kPcMaxB + b) * 8));
-        hit = true;
-      }
-    }
+    for (int q = 0; q < 4; q++) rr[q] = pc_take<L>(S, ww[q], cc[q], mm[q], b, act, ub, cu, A, hit);
     if (L >= 5) {
 #pragma unroll
-      for (int q = 0; q < 4; q++)
-        if (cc[q] >= 0) pc_add_row_dyn<L>(P, rr[q], cc[q]);
+      for (int q = 0; q < 4; q++) pc_add_row_dyn<L>(P, rr[q], cc[q]);
     }
+  }
+  while (m) {
+    const int t = __ffs(m) - 1;
+    m &= m - 1u;
+    const int32_t w = __shfl_sync(FULL, k.w, t);
+    const int c = __shfl_sync(FULL, k.c, t);
+    const unsigned long long mm = __shfl_sync(FULL, k.m, t);
+    const uint4 r = pc_take<L>(S, w, c, mm, b, act, ub, cu, A, hit);
+    if (L >= 5) pc_add_row_dyn<L>(P, r, c);
   }
 }
 
@@ -360,6 +378,10 @@ __device__ __forceinline__ void pc_meet(const uint32_t *tag, const PcScratch &S,
   constexpr int NP = L * (L - 1) / 2;
   constexpr unsigned FULL = 0xffffffffu;
   const bool act = active && x < ub && cx != cu;
+  // the row is rank ordered: past the highest source, nothing further counts
+  bool past = __any_sync(FULL, k.w >= umax);
+  unsigned m = pc_members<L>(k);
+  if (!m && (past || deg <= 32)) return;  // x meets no member
   if (!__any_sync(FULL, act)) return;
   uint32_t A[L], P[NP];
 #pragma unroll
@@ -368,12 +390,12 @@ __device__ __forceinline__ void pc_meet(const uint32_t *tag, const PcScratch &S,
   for (int j = 0; j < NP; j++) P[j] = 0;
   bool hit = false;
   for (int base = 0;;) {
-    // the row is rank ordered: past the highest source, nothing further counts
-    const bool past = __any_sync(FULL, k.w >= umax);
-    pc_visit_chunk<L>(S, k, lane, act, ub, cu, A, P, hit);
+    pc_visit_chunk<L>(S, k, m, lane, act, ub, cu, A, P, hit);
     base += 32;
     if (past || base >= deg) break;
     k = pc_load_chunk(tag, S, xb, deg, base + lane, cx, umax);
+    past = __any_sync(FULL, k.w >= umax);
+    m = pc_members<L>(k);
   }
   if (!act || !hit) return;
   // free colours f0 < f1 < ... (all but chi(u) and chi(x))
@@ -437,39 +459,43 @@ __global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const ui
 }
 
 // --------------------------- clear and finish ---------------------------
+// grid.y = source b: zero its level-1 membership words and, for its listed
+// level-2 vertices, the membership word, the row and the list entry.
 template <int L>
-__global__ void k_pc_clear(GraphView g, const uint8_t *colors, PcScratch S, PcGroup G) {
+__global__ void k_pc_clear(GraphView g, PcScratch S, PcGroup G) {
+  const int b = blockIdx.y;
   const int64_t n = g.n;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nt = (int64_t)gridDim.x * blockDim.x;
-  for (int b = 0; b < G.B; b++) {
-    const int32_t u = G.u[b];
-    const int64_t ub = g.row[u];
-    const int du = g.lo_cnt[u];
-    for (int64_t i = t0; i < du; i += nt) S.member[__ldg(g.col + ub + i)] = 0;
-    if (L >= 5) {
-      const int cnt = S.cnt[b];
-      for (int64_t i = t0; i < cnt; i += nt) {
-        const int32_t w = S.list[(int64_t)b * n + i];
-        S.list[(int64_t)b * n + i] = 0;
-        S.member[w] = 0;
-        *(uint4 *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8) = make_uint4(0, 0, 0, 0);
-      }
+  const int32_t u = G.u[b];
+  const int64_t ub = g.row[u];
+  const int du = g.lo_cnt[u];
+  for (int64_t i = t0; i < du; i += nt) S.member[__ldg(g.col + ub + i)] = 0;
+  if (L >= 5) {
+    const int cnt = S.cnt[b];
+    for (int64_t i = t0; i < cnt; i += nt) {
+      const int32_t w = S.list[(int64_t)b * n + i];
+      S.list[(int64_t)b * n + i] = 0;
+      S.member[w] = 0;
+      *(uint4 *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8) = make_uint4(0, 0, 0, 0);
     }
   }
-  (void)colors;
 }
 
+// One lane per source: the group's totals (times the rotation multiplier)
+// into the per-vertex split and the count; totals and list counts back to 0.
 __global__ void k_pc_finish(PcScratch S, PcGroup G, int multiplier, u64 *per_vertex, u64 *status) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int b = threadIdx.x;
   unsigned ovf = 0;
-  for (int b = 0; b < G.B; b++) {
-    u64 t = mul_ck(S.totals[b], (u64)multiplier, ovf);
+  u64 t = 0;
+  if (b < G.B) {
+    t = mul_ck(S.totals[b], (u64)multiplier, ovf);
     S.totals[b] = 0;
     S.cnt[b] = 0;
     if (per_vertex) per_vertex[G.u[b]] = t;
-    atomic_add_ck(status + ST_COUNT, t, ovf);
   }
+  t = warp_sum_ck(t, ovf);
+  if (b == 0 && t) atomic_add_ck(status + ST_COUNT, t, ovf);
   flag_overflow(status, ovf);
 }
 
@@ -775,7 +801,7 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
     k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S, G, a.colors, a.status);
     c.kernels++;
     timing_end(c);
-    k_pc_clear<L><<<sms, 256, 0, c.stream>>>(a.g, a.colors, S, G);
+    k_pc_clear<L><<<dim3(std::max(1, sms / 8), G.B), 256, 0, c.stream>>>(a.g, S, G);
     c.kernels++;
     k_pc_finish<<<1, 32, 0, c.stream>>>(S, G, a.multiplier, a.per_vertex, a.status);
     c.kernels++;
