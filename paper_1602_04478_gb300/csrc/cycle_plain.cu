@@ -468,87 +468,6 @@ __global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const ui
   flag_overflow(status, ovf);
 }
 
-// The same pull for groups whose members are sparse: one warp per block of
-// 32 consecutive meeting vertices, whose rows are contiguous in the
-// adjacency and are scanned together, 32 entries at a time.  Each lane finds
-// the vertex its entry belongs to among the block's row starts (held one
-// per lane); the members of a chunk are visited vertex by vertex in rank
-// order, and a vertex's closure runs when the visit moves past it.  One
-// chain of loads thus serves several low-degree meeting vertices.
-template <int L>
-__global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull_blocks(GraphView g, const uint32_t *tag, PcScratch S,
-                                                               PcGroup G, const uint8_t *colors, u64 *status) {
-  constexpr int NP = L * (L - 1) / 2;
-  constexpr unsigned FULL = 0xffffffffu;
-  __shared__ uint32_t sP[L >= 5 ? NP : 1][kPcThreads];
-  __shared__ uint32_t sA[L <= 5 ? L : 1][kPcThreads];
-  const int tid = threadIdx.x, lane = tid & 31, b = lane;
-  const bool active = b < G.B;
-  const int32_t ub = active ? G.u[b] : -1;
-  const int cu = active ? colors[ub] : -1;
-  const int32_t umax = G.umax;
-  u64 tot = 0;
-  unsigned ovf = 0;
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t x0 = warp0 * 32; x0 < umax; x0 += nwarps * 32) {
-    const int nx = (int)(umax - x0 < 32 ? umax - x0 : 32);
-    const int64_t e_end = g.row[x0 + nx];
-    const int64_t rs = lane < nx ? g.row[x0 + lane] : e_end;  // row start of x0 + lane
-    const int cxl = lane < nx ? colors[x0 + lane] : 0;
-    const int64_t e_beg = __shfl_sync(FULL, rs, 0);
-    int cur = -1;  // block index of the vertex whose sums are open
-    int cx = 0;
-    bool act = false, hit = false;
-    uint32_t A[L], P[NP];
-#pragma unroll
-    for (int c = 0; c < L; c++) A[c] = 0;
-#pragma unroll
-    for (int j = 0; j < NP; j++) P[j] = 0;
-    for (int64_t eb = e_beg; eb < e_end; eb += 32) {
-      const int64_t e = eb + lane;
-      // block index of the vertex owning entry e: the last row start <= e
-      int xi = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int cand = xi + step;
-        const int64_t r = __shfl_sync(FULL, rs, cand & 31);
-        if (cand < nx && r <= e) xi = cand;
-      }
-      const int cxe = __shfl_sync(FULL, cxl, xi);
-      PcChunk k;
-      const uint32_t t = e < e_end ? __ldg(tag + e) : 0xFFFFFFFFu;
-      k.w = e < e_end ? (int32_t)(t & kTagMask) : INT32_MAX;
-      k.c = k.w < umax ? (int)(t >> kTagShift) : cxe;
-      const bool any = k.c != cxe && ((__ldg(S.anym + (k.w >> 5)) >> (k.w & 31)) & 1u);
-      k.m = any ? __ldg(S.member + k.w) : 0ull;
-      unsigned m = pc_members<L>(k);
-      while (m) {
-        const int xt = __shfl_sync(FULL, xi, __ffs(m) - 1);
-        const unsigned mx = m & __ballot_sync(FULL, xi == xt);
-        m &= ~mx;
-        if (xt != cur) {
-          if (cur >= 0) {
-            pc_close_x<L>(A, P, act && hit, cu, cx, sA, sP, tid, tot, ovf);
-#pragma unroll
-            for (int c = 0; c < L; c++) A[c] = 0;
-#pragma unroll
-            for (int j = 0; j < NP; j++) P[j] = 0;
-          }
-          cur = xt;
-          cx = __shfl_sync(FULL, cxl, xt);
-          act = active && (int32_t)(x0 + xt) < ub && cx != cu;
-          hit = false;
-        }
-        pc_visit_chunk<L>(S, k, mx, b, act, ub, cu, A, P, hit);
-      }
-    }
-    if (cur >= 0) pc_close_x<L>(A, P, act && hit, cu, cx, sA, sP, tid, tot, ovf);
-  }
-  if (active && tot) atomic_add_ck(S.totals + b, tot, ovf);
-  flag_overflow(status, ovf);
-}
-
 // --------------------------- clear and finish ---------------------------
 // grid.y = source b: zero its level-1 membership words and, for its listed
 // level-2 vertices, the membership word, the row and the list entry.
@@ -889,12 +808,7 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
     }
     timing_end(c);
     timing_begin(c, "cycle_plain_pull");
-    // dense members (the groups of the pull-form build): one warp per
-    // meeting vertex; sparse members: blocks of 32 meeting vertices per warp
-    if (use_pull)
-      k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S, G, a.colors, a.status);
-    else
-      k_pc_pull_blocks<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S, G, a.colors, a.status);
+    k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S, G, a.colors, a.status);
     c.kernels++;
     timing_end(c);
     k_pc_clear<L><<<dim3(std::max(1, sms / 8), G.B), 256, 0, c.stream>>>(a.g, S, G);
