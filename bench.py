@@ -39,6 +39,7 @@ UNIT = "G edge-subset updates/s"
 WORKLOAD = {"graph": "chung_lu", "n": 1_000_000, "mean_deg": 16, "gamma": 2.1, "seed": 2,
             "queries": ["C6", "glasses"], "form": "plain", "colourings_per_query_per_step": 1}
 COLOR_SEED = 1
+BATCH_QUERIES = ["C5", "chord_pendant", "glasses"]
 FLUSH_BYTES = 256 << 20
 
 
@@ -297,6 +298,8 @@ def main():
     ap.add_argument("--serve-small", action="store_true", help="one n = 1e6 graph instead of nine")
     ap.add_argument("--serve-budget", type=int, default=64, help="server table budget in GiB")
     ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--batch-trials", type=int, default=64,
+                    help="colourings per query in the batched-configuration leg (0: skip it)")
     ap.add_argument("--heavy-degree", type=int, default=-1,
                     help="heavy/light source degree threshold (default: autotuned)")
     ap.add_argument("--profile-case", default=None, metavar="QUERY",
@@ -415,6 +418,42 @@ def main():
                "ms_per_step": 1e3 * batched_s / args.steps, "timing": "host clock around synchronous calls",
                "form": f"{len(qids)} requests x {args.steps} colourings per cc_count_batch call, CUDA-graph replay"}
 
+    # the batched configuration: T colourings x 3 queries (C5, 4-cycle with a
+    # chord and a pendant, glasses) on the same graph in one cc_count_batch
+    # call replayed as a CUDA graph, against the same colourings counted one
+    # cc_count call per colouring (a subset of them, to keep the leg short)
+    batch_cfg = None
+    if args.batch_trials > 0:
+        q3 = {name: ctx.set_query(*gg.query(name)) for name in BATCH_QUERIES}
+        if args.heavy_degree < 0:
+            for q in q3.values():
+                P.cc_autotune(ctx.h, gid, q)
+        T3 = args.batch_trials
+        first3 = trial_base + 30_000
+        reqs3 = [(gid, q, first3, T3) for q in q3.values()]
+        P.cc_count_batch(ctx.h, reqs3)  # eager run + capture (untimed)
+        barrier()
+        t0 = time.perf_counter()
+        res3, st3 = P.cc_count_batch(ctx.h, reqs3)
+        barrier()
+        b3 = time.perf_counter() - t0
+        Tp = min(T3, 8)
+        plain3 = {}
+        barrier()
+        t0 = time.perf_counter()
+        for name, q in q3.items():
+            plain3[name] = [int(ctx.count(gid, q, first3 + t, 1)[0][0]) for t in range(Tp)]
+        barrier()
+        p3 = time.perf_counter() - t0
+        equal = all([int(x) for x in res3[i][:Tp]] == plain3[name] for i, name in enumerate(q3))
+        batch_cfg = {"workload": f"{workload_name()}; {T3} colourings x {len(q3)} queries per cc_count_batch call",
+                     "queries": list(q3), "trials": T3,
+                     "colorings_per_s_batched": len(q3) * T3 * world / b3,
+                     "colorings_per_s_plain": len(q3) * Tp * world / p3,
+                     "ms_batched_call": 1e3 * b3, "plain_trials_timed": Tp,
+                     "counts_equal_batched_vs_plain": bool(equal), "status": st3,
+                     "timing": "host clock around synchronous calls; batched = CUDA-graph replay of all passes"}
+
     # end to end through the C-ABI with host buffers: load the CSR from host
     # memory, count both queries, read the counts back, free the graph
     e2e_steps = max(1, min(args.steps, 3))
@@ -437,7 +476,8 @@ def main():
             "config": {"workload": workload_name(), **WORKLOAD, "parallelism": f"replicas x{world}",
                        "l2": "256 MB flush between steps, outside the events; working set > L2",
                        "units_per_step": units_step, "units_by_query": units},
-            "colorings_per_s": colourings, "wall_s": wall, "batched": batched, "heavy_degree": tuned,
+            "colorings_per_s": colourings, "wall_s": wall, "batched": batched, "batched_config": batch_cfg,
+            "heavy_degree": tuned,
             "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kern.items()},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks, "e2e": e2e,
             "counts_first_step": counts[0] if counts else None}
