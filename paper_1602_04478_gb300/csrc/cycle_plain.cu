@@ -561,14 +561,20 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
         const int32_t v = __ldg(g.col + ub + i);
         const int cv = colors[v];
         if (cv == cu) continue;
-        const int64_t vb = g.row[v];
-        const int64_t ve = lower_bound_i32(g.col, vb, g.row[v + 1], u);
-        for (int64_t e = vb + lane; e < ve; e += 32) {
-          const int32_t w = __ldg(g.col + e);
-          const int cw = colors[w];
-          if (cw == cu || cw == cv) continue;
-          atomicAdd(W2 + (int64_t)w * 8 + cv, 1u);
-          if (!(atomicOr(mark + w, 1u) & 1u)) L2[atomicAdd(&s_n2, 1)] = w;
+        // v's row is rank ordered: walk it to the first chunk that reaches u
+        const int64_t vb = g.row[v], vend = g.row[v + 1];
+        for (int64_t e0 = vb; e0 < vend; e0 += 32) {
+          const int64_t e = e0 + lane;
+          const int32_t w = e < vend ? __ldg(g.col + e) : INT32_MAX;
+          const bool done = __any_sync(0xffffffffu, w >= u);
+          if (w < u) {
+            const int cw = colors[w];
+            if (cw != cu && cw != cv) {
+              atomicAdd(W2 + (int64_t)w * 8 + cv, 1u);
+              if (!(atomicOr(mark + w, 1u) & 1u)) L2[atomicAdd(&s_n2, 1)] = w;
+            }
+          }
+          if (done) break;
         }
       }
       __syncthreads();
@@ -581,21 +587,26 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
           const uint4 r0 = *(const uint4 *)(W2 + (int64_t)w * 8);
           const uint4 r1 = *(const uint4 *)(W2 + (int64_t)w * 8 + 4);
           const uint32_t row[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-          const int64_t wb = g.row[w];
-          const int64_t we = lower_bound_i32(g.col, wb, g.row[w + 1], u);
-          for (int64_t e = wb + lane; e < we; e += 32) {
-            const int32_t x = __ldg(g.col + e);
-            const int cx = colors[x];
-            if (cx == cu || cx == cw) continue;
-            bool any = false;
+          const int64_t wb = g.row[w], wend = g.row[w + 1];
+          for (int64_t e0 = wb; e0 < wend; e0 += 32) {
+            const int64_t e = e0 + lane;
+            const int32_t x = e < wend ? __ldg(g.col + e) : INT32_MAX;
+            const bool done = __any_sync(0xffffffffu, x >= u);
+            if (x < u) {
+              const int cx = colors[x];
+              if (cx != cu && cx != cw) {
+                bool any = false;
 #pragma unroll
-            for (int c = 0; c < 8; c++) {
-              const uint32_t t = row[c];
-              if (!t || c == cx) continue;
-              atomicAdd(W3 + (int64_t)x * 16 + pair_idx(cw, c), t);
-              any = true;
+                for (int c = 0; c < 8; c++) {
+                  const uint32_t t = row[c];
+                  if (!t || c == cx) continue;
+                  atomicAdd(W3 + (int64_t)x * 16 + pair_idx(cw, c), t);
+                  any = true;
+                }
+                if (any && !(atomicOr(mark + x, 2u) & 2u)) L3[atomicAdd(&s_n3, 1)] = x;
+              }
             }
-            if (any && !(atomicOr(mark + x, 2u) & 2u)) L3[atomicAdd(&s_n3, 1)] = x;
+            if (done) break;
           }
         }
         __syncthreads();

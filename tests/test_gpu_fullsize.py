@@ -3,9 +3,11 @@ exponent 2.1) in the configuration bench.py times.
 
 * C6: the count split by highest cycle vertex; sampled sources are checked
   one by one against the oracle restricted to those sources.
-* glasses: the oracle cannot build its tables over the whole graph in test
-  time, so properties that hold at any size are checked: the count is the
-  same for different decomposition orders and for a relabelled graph.
+* C5 (the batched configuration's cycle query): sampled sources, as for C6.
+* glasses and the 4-cycle with a chord and a pendant: the oracle cannot
+  build their tables over the whole graph in test time, so properties that
+  hold at any size are checked: the count is the same for different
+  decomposition orders and for a relabelled graph.
 """
 import numpy as np
 import pytest
@@ -50,6 +52,37 @@ def test_c6_sampled_sources_match_oracle(big):
     for v in pick:
         assert int(pv[v]) == per[v], int(v)
     P.cc_set_heavy_degree(ctx.h, -1)
+
+
+def test_c5_sampled_sources_match_oracle(big):
+    P, ctx, g, gid = big
+    k, e = gg.query("C5")
+    P.cc_set_coloring_seed(ctx.h, 3)
+    qid = ctx.set_query(k, e)
+    pv, total = ctx.count_per_vertex(gid, qid, 0)
+    assert int(pv.sum()) == total
+    deg = np.diff(g.row_ptr)
+    rng = np.random.default_rng(1)
+    pick = np.concatenate([rng.choice(np.flatnonzero((deg >= 8) & (deg <= 64)), size=12, replace=False),
+                           rng.choice(np.flatnonzero((deg >= 200) & (deg <= 260)), size=2, replace=False)])
+    filt = np.zeros(g.n, dtype=np.uint8)
+    filt[pick] = 1
+    _, _, per = O.dp_count(g, k, e, O.colors(3, 0, g.n, k), root_filter=filt, per_source=True)
+    for v in pick:
+        assert int(pv[v]) == per[v], int(v)
+
+
+def test_chord_pendant_decomposition_invariant_at_full_size(big):
+    P, ctx, g, gid = big
+    k, e = gg.query("chord_pendant")
+    P.cc_set_coloring_seed(ctx.h, 2)
+    orders = [[0, 1, 4, 3, 0, 1, 2], [3, 0, 2, 3, 0, 1, 4], [0, 1, 4, 3, 0, 2, 3]]
+    got = []
+    for seq in orders:
+        qid = ctx.set_query(k, e)
+        P.cc_set_decomposition(ctx.h, qid, seq)
+        got.append([int(x) for x in ctx.count(gid, qid, 0, 2)[0]])
+    assert got[0] == got[1] == got[2] and got[0][0] > 0
 
 
 def test_glasses_decomposition_invariant_at_full_size(big):
