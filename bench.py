@@ -247,6 +247,8 @@ def run_serve(args):
     cap = len(burst) / (time.perf_counter() - t0)
     out = {"impl": "ours", "mode": "serve", "graphs": len(graphs), "queries": qnames,
            "capacity_req_per_s": cap, "requests_per_rate": args.serve_requests, "rates": []}
+    # progress lines (a cut-off run still leaves its measurements); the last line is the summary
+    print(json.dumps({**out, "partial": True}), flush=True)
     for frac in (0.7, 1.0):
         lam = frac * cap
         arrivals = np.cumsum(rng.exponential(1.0 / lam, size=args.serve_requests))
@@ -263,6 +265,7 @@ def run_serve(args):
         out["rates"].append({"load": frac, "lambda_req_per_s": lam, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                              "p99_ms": 1e3 * float(np.percentile(lat, 99)), "req_per_s": len(reqs) / wall,
                              "colorings_per_s": colourings / wall})
+        print(json.dumps({**out, "partial": True}), flush=True)
     srv.close()
     print(json.dumps(out), flush=True)
     return 0
