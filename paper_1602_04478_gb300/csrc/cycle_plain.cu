@@ -709,8 +709,29 @@ int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank) {
   S.o_l2 = take((size_t)n * 4);
   S.o_l3 = a.L >= 5 ? take((size_t)n * 4) : 0;
   S.slot_bytes = off;
-  size_t budget = c.budget ? (c.budget > c.in_use ? (c.budget - c.in_use) / 2 : 0) : ((size_t)16 << 30);
-  int slots = (int)std::min<size_t>(152 * 2, budget / std::max<size_t>(1, S.slot_bytes));
+  // one slot per resident CTA (up to four per SM); without a budget, slots
+  // take at most a quarter of the free device memory and 64 GiB.  A scratch
+  // already large enough for more slots is used whole, and under stream
+  // capture only the scratch at hand is used (no allocation).
+  constexpr int kMaxSlots = 152 * 4;
+  const size_t have = c.scratch_bytes > 256 ? (c.scratch_bytes - 256) / std::max<size_t>(1, S.slot_bytes) : 0;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(c.stream, &cs) != cudaSuccess) return CC_ERR_CUDA;
+  int slots;
+  if (cs != cudaStreamCaptureStatusNone && have >= 1) {
+    slots = (int)std::min<size_t>(kMaxSlots, have);
+  } else {
+    size_t budget;
+    if (c.budget) {
+      budget = c.budget > c.in_use ? (c.budget - c.in_use) / 2 : 0;
+    } else {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return CC_ERR_CUDA;
+      budget = std::min<size_t>(fr / 4, (size_t)64 << 30);
+    }
+    slots = (int)std::max<size_t>(std::min<size_t>(kMaxSlots, budget / std::max<size_t>(1, S.slot_bytes)),
+                                  std::min<size_t>(kMaxSlots, have));
+  }
   if (slots < 1) return CC_ERR_OOM;
   size_t need = (size_t)slots * S.slot_bytes + 256;
   int rc = ensure_scratch(c, need);
