@@ -468,6 +468,48 @@ __global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const ui
   flag_overflow(status, ovf);
 }
 
+// Two groups in one pass over the meeting vertices (groups A and B, A the
+// higher, each with its own scratch bank and a member map shared by both):
+// the scan of x -- row bounds, the first chunk of tagged neighbours, the
+// member map -- is paid once for 64 sources; each group is then visited and
+// closed as in k_pc_pull (lane b = source b of A, then of B).
+template <int L>
+__global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull2(GraphView g, const uint32_t *tag, PcScratch SA, PcGroup GA,
+                                                         PcScratch SB, PcGroup GB, const uint8_t *colors,
+                                                         u64 *status) {
+  constexpr int NP = L * (L - 1) / 2;
+  __shared__ uint32_t sP[L >= 5 ? NP : 1][kPcThreads];
+  __shared__ uint32_t sA[L <= 5 ? L : 1][kPcThreads];
+  const int tid = threadIdx.x, lane = tid & 31, b = lane;
+  const bool actA = b < GA.B, actB = b < GB.B;
+  const int32_t ubA = actA ? GA.u[b] : -1, ubB = actB ? GB.u[b] : -1;
+  const int cuA = actA ? colors[ubA] : -1, cuB = actB ? colors[ubB] : -1;
+  const int32_t umax = GA.umax;
+  u64 totA = 0, totB = 0;
+  unsigned ovf = 0;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t xi = warp0; xi < umax; xi += nwarps) {
+    const int32_t x = (int32_t)xi;
+    const int cx = colors[x];
+    const int64_t xb = g.row[x];
+    const int deg = (int)(g.row[x + 1] - xb);
+    const uint32_t t = lane < deg ? __ldg(tag + xb + lane) : 0xFFFFFFFFu;
+    PcChunk kA;
+    kA.w = lane < deg ? (int32_t)(t & kTagMask) : INT32_MAX;
+    kA.c = kA.w < umax ? (int)(t >> kTagShift) : cx;
+    const bool any = kA.c != cx && ((__ldg(SA.anym + (kA.w >> 5)) >> (kA.w & 31)) & 1u);
+    kA.m = any ? __ldg(SA.member + kA.w) : 0ull;
+    PcChunk kB = kA;
+    kB.m = any ? __ldg(SB.member + kA.w) : 0ull;
+    pc_meet<L>(tag, SA, x, cx, xb, deg, kA, lane, actA, ubA, cuA, umax, sA, sP, tid, totA, ovf);
+    pc_meet<L>(tag, SB, x, cx, xb, deg, kB, lane, actB, ubB, cuB, umax, sA, sP, tid, totB, ovf);
+  }
+  if (actA && totA) atomic_add_ck(SA.totals + b, totA, ovf);
+  if (actB && totB) atomic_add_ck(SB.totals + b, totB, ovf);
+  flag_overflow(status, ovf);
+}
+
 // --------------------------- clear and finish ---------------------------
 // grid.y = source b: zero its level-1 membership words and, for its listed
 // level-2 vertices, the membership word, the row and the list entry.
@@ -791,28 +833,46 @@ static int push_work(Ctx &c, const GraphView &g, const int64_t **out) {
 constexpr double kPullLevelsRatio = 0.7;
 
 template <int L>
-static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcScratch &S, const uint32_t *tag) {
+static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcScratch *SB, const uint32_t *tag) {
   const int64_t n = a.g.n;
   const int sms = 152;
+  const PcScratch &S0 = SB[0], &S1 = SB[1];
   const int64_t *pw = nullptr;
   if (L >= 5) {
     int rc = push_work(c, a.g, &pw);
     if (rc != CC_OK) return rc;
   }
+  // groups of the pull-form level build use bank 0 and leave it to be zeroed
   auto zero_levels = [&]() {
-    return cudaMemsetAsync(S.member, 0, (size_t)n * 8, c.stream) == cudaSuccess &&
-           cudaMemsetAsync(S.w2, 0, (size_t)kPcMaxB * n * 16, c.stream) == cudaSuccess;
+    return cudaMemsetAsync(S0.member, 0, (size_t)n * 8, c.stream) == cudaSuccess &&
+           cudaMemsetAsync(S0.w2, 0, (size_t)kPcMaxB * n * 16, c.stream) == cudaSuccess;
+  };
+  auto group_at = [&](int64_t top) {
+    PcGroup G;
+    G.B = (int)std::min<int64_t>(kPcMaxB, top - first_rank + 1);
+    G.umax = (int32_t)top;
+    for (int b = 0; b < G.B; b++) G.u[b] = (int32_t)(top - b);
+    return G;
+  };
+  auto push_levels = [&](const PcScratch &S, const PcGroup &G) {
+    const int64_t du = c.cur_graph_row[G.umax + 1] - c.cur_graph_row[G.umax];
+    dim3 gl((unsigned)std::max<int64_t>(1, std::min<int64_t>(sms * 2, (du * 32 + kPcThreads - 1) / kPcThreads)),
+            G.B);
+    k_pc_levels<L><<<gl, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G);
+    c.kernels++;
+  };
+  auto close_group = [&](const PcScratch &S, const PcGroup &G) {
+    k_pc_clear<L><<<dim3(std::max(1, sms / 8), G.B), 256, 0, c.stream>>>(a.g, S, G);
+    c.kernels++;
+    k_pc_finish<<<1, 32, 0, c.stream>>>(S, G, a.multiplier, a.per_vertex, a.status);
+    c.kernels++;
   };
   const size_t anym_bytes = (size_t)((n + 31) / 32) * 4;
   k_tag_cols<<<sms * 8, 256, 0, c.stream>>>(a.g, a.colors, (uint32_t *)tag);
   c.kernels++;
   bool pulled = false, pushed = false;
-  for (int64_t top = n - 1; top >= first_rank; top -= kPcMaxB) {
-    PcGroup G;
-    G.B = (int)std::min<int64_t>(kPcMaxB, top - first_rank + 1);
-    G.umax = (int32_t)top;
-    for (int b = 0; b < G.B; b++) G.u[b] = (int32_t)(top - b);
-    int64_t du = c.cur_graph_row[top + 1] - c.cur_graph_row[top];
+  for (int64_t top = n - 1; top >= first_rank;) {
+    const PcGroup G = group_at(top);
     // the pull form serves a prefix of the groups (the highest sources)
     bool use_pull = false;
     if (pw && !pushed) {
@@ -821,36 +881,48 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
       use_pull = work > kPullLevelsRatio * (double)c.cur_graph_row[top];
     }
     if (!use_pull && pulled && !pushed && !zero_levels()) return CC_ERR_CUDA;
-    // the one-bit member map is rebuilt for every group
-    if (cudaMemsetAsync(S.anym, 0, anym_bytes, c.stream) != cudaSuccess) return CC_ERR_CUDA;
-    timing_begin(c, use_pull ? "cycle_plain_levels_pull" : "cycle_plain_levels");
+    // the one-bit member map is rebuilt for every pass
+    if (cudaMemsetAsync(S0.anym, 0, anym_bytes, c.stream) != cudaSuccess) return CC_ERR_CUDA;
     if (use_pull) {
+      const int64_t du = c.cur_graph_row[top + 1] - c.cur_graph_row[top];
+      timing_begin(c, "cycle_plain_levels_pull");
       dim3 gm((unsigned)std::max<int64_t>(1, std::min<int64_t>(sms, (du + kPcThreads - 1) / kPcThreads)), G.B);
-      k_pc_mark1<<<gm, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G, L <= 5);
+      k_pc_mark1<<<gm, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G, L <= 5);
       c.kernels++;
-      k_pc_levels_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G);
+      k_pc_levels_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G);
       c.kernels++;
+      timing_end(c);
+      timing_begin(c, "cycle_plain_pull");
+      k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S0, G, a.colors, a.status);
+      c.kernels++;
+      timing_end(c);
+      close_group(S0, G);
       pulled = true;
-    } else {
-      dim3 gl((unsigned)std::max<int64_t>(1, std::min<int64_t>(sms * 2, (du * 32 + kPcThreads - 1) / kPcThreads)),
-              G.B);
-      k_pc_levels<L><<<gl, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G);
-      c.kernels++;
-      pushed = true;
+      top -= kPcMaxB;
+      continue;
     }
+    // push form: two groups per pass when two remain
+    pushed = true;
+    const bool two = top - kPcMaxB >= first_rank;
+    const PcGroup G2 = two ? group_at(top - kPcMaxB) : G;
+    timing_begin(c, "cycle_plain_levels");
+    push_levels(S0, G);
+    if (two) push_levels(S1, G2);
     timing_end(c);
     timing_begin(c, "cycle_plain_pull");
-    k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S, G, a.colors, a.status);
+    if (two)
+      k_pc_pull2<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S0, G, S1, G2, a.colors, a.status);
+    else
+      k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S0, G, a.colors, a.status);
     c.kernels++;
     timing_end(c);
-    k_pc_clear<L><<<dim3(std::max(1, sms / 8), G.B), 256, 0, c.stream>>>(a.g, S, G);
-    c.kernels++;
-    k_pc_finish<<<1, 32, 0, c.stream>>>(S, G, a.multiplier, a.per_vertex, a.status);
-    c.kernels++;
+    close_group(S0, G);
+    if (two) close_group(S1, G2);
+    top -= two ? 2 * kPcMaxB : kPcMaxB;
   }
   // the scratch is all zero between launches
   if (pulled && !pushed && !zero_levels()) return CC_ERR_CUDA;
-  if (cudaMemsetAsync(S.anym, 0, anym_bytes, c.stream) != cudaSuccess) return CC_ERR_CUDA;
+  if (cudaMemsetAsync(S0.anym, 0, anym_bytes, c.stream) != cudaSuccess) return CC_ERR_CUDA;
   return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }
 
@@ -871,23 +943,30 @@ int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank) {
     return o;
   };
   const bool lv2 = a.L >= 5;
-  size_t o_w2 = lv2 ? take((size_t)kPcMaxB * n * 8 * 2) : 0;
-  size_t o_mem = take((size_t)n * 8);
-  size_t o_list = lv2 ? take((size_t)kPcMaxB * n * 4) : 0;
-  size_t o_cnt = take(kPcMaxB * 4);
-  size_t o_tot = take(kPcMaxB * 8);
+  // two banks of per-group scratch (two groups pulled together) and one
+  // member map shared by them
+  size_t o_w2[2], o_mem[2], o_list[2], o_cnt[2], o_tot[2];
+  for (int k = 0; k < 2; k++) {
+    o_w2[k] = lv2 ? take((size_t)kPcMaxB * n * 8 * 2) : 0;
+    o_mem[k] = take((size_t)n * 8);
+    o_list[k] = lv2 ? take((size_t)kPcMaxB * n * 4) : 0;
+    o_cnt[k] = take(kPcMaxB * 4);
+    o_tot[k] = take(kPcMaxB * 8);
+  }
   size_t o_anym = take((size_t)((n + 31) / 32) * 4);
   size_t need = off;
   int rc0 = ensure_hv_scratch(c, need);
   if (rc0 != CC_OK) return rc0;
   char *base = (char *)c.hv_scratch;
-  PcScratch S;
-  S.w2 = (uint16_t *)(base + o_w2);
-  S.member = (unsigned long long *)(base + o_mem);
-  S.list = (int32_t *)(base + o_list);
-  S.cnt = (int *)(base + o_cnt);
-  S.totals = (u64 *)(base + o_tot);
-  S.anym = (uint32_t *)(base + o_anym);
+  PcScratch S[2];
+  for (int k = 0; k < 2; k++) {
+    S[k].w2 = (uint16_t *)(base + o_w2[k]);
+    S[k].member = (unsigned long long *)(base + o_mem[k]);
+    S[k].list = (int32_t *)(base + o_list[k]);
+    S[k].cnt = (int *)(base + o_cnt[k]);
+    S[k].totals = (u64 *)(base + o_tot[k]);
+    S[k].anym = (uint32_t *)(base + o_anym);
+  }
   // the tagged adjacency is rewritten every pass: it lives outside the
   // heavy scratch, whose contents are zero between launches
   if ((rc0 = ensure_tag_scratch(c, (size_t)std::max<int64_t>(a.g.nnz, 1) * 4)) != CC_OK) return rc0;
