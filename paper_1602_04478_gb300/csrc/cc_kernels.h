@@ -91,7 +91,7 @@ int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank);
 struct PlScratch {
   char *base;
   size_t slot_bytes;
-  size_t o_w2, o_w3, o_mark, o_l2, o_l3;
+  size_t o_w2, o_w3, o_mark, o_id3, o_l2, o_l3;  // rows by local index; ids by vertex; lists
 };
 int launch_pc_light_raw(cudaStream_t stream, int L, const GraphView &g, const uint8_t *colors, const PlScratch &S,
                         int slots, int32_t end_rank, int *work, u64 *status, int k);

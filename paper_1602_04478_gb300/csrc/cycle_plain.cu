@@ -558,9 +558,14 @@ __global__ void k_pc_finish(PcScratch S, PcGroup G, int multiplier, u64 *per_ver
 // colours), and the closure runs over the touched meeting vertices only.
 // u32 is exact here: a level-3 entry counts paths u-v-w-x and is at most
 // deg(x) * deg(u), which the host checks stays below 2^32.
+//
+// The rows of one source are compact: a vertex reached at level 2 (3) gets
+// the next local index, and its row lives at that index, so the rows a source
+// touches are contiguous and stay in cache.  Each level is walked twice: the
+// first walk claims the vertices (id[v] = -1 marks a claim, the claimant
+// lists it), the CTA then numbers the list (id[v] = index + 1), and the second
+// walk adds into the numbered rows.
 constexpr int kPlThreads = 256;
-
-
 
 __device__ __forceinline__ int pair_idx(int a, int b) {
   int hi = a > b ? a : b, lo = a > b ? b : a;
@@ -571,14 +576,16 @@ template <int L>
 __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint8_t *colors, PlScratch S,
                                                          int32_t end_rank, int *work, int multiplier,
                                                          u64 *per_vertex, u64 *status, int k) {
+  constexpr unsigned FULL = 0xffffffffu;
   __shared__ int s_u, s_n2, s_n3;
   __shared__ unsigned long long s_tot;
   __shared__ unsigned s_ovf;
   char *slot = S.base + (size_t)blockIdx.x * S.slot_bytes;
-  uint32_t *W2 = (uint32_t *)(slot + S.o_w2);   // [n][8] by colour
-  uint32_t *W3 = (uint32_t *)(slot + S.o_w3);   // [n][16] by colour pair
-  uint32_t *mark = (uint32_t *)(slot + S.o_mark);
-  int32_t *L2 = (int32_t *)(slot + S.o_l2);
+  uint32_t *W2 = (uint32_t *)(slot + S.o_w2);   // [local][8] level-2 rows by colour of v
+  uint32_t *W3 = (uint32_t *)(slot + S.o_w3);   // [local][16] level-3 rows by colour pair
+  int32_t *id2 = (int32_t *)(slot + S.o_mark);  // [n] local index + 1 at level 2 (0 none, -1 claimed)
+  int32_t *id3 = (int32_t *)(slot + S.o_id3);   // [n] the same at level 3
+  int32_t *L2 = (int32_t *)(slot + S.o_l2);     // local index -> vertex
   int32_t *L3 = (int32_t *)(slot + S.o_l3);
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   constexpr int NW = kPlThreads / 32;
@@ -598,68 +605,87 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
     const int du = g.lo_cnt[u];
     unsigned ovf = 0;
     if (du >= 2) {
-      // level 2: W2[w][chi(v)] over v in N<(u), w in N<u(v)
-      for (int i = wib; i < du; i += NW) {
-        const int32_t v = __ldg(g.col + ub + i);
-        const int cv = colors[v];
-        if (cv == cu) continue;
-        // v's row is rank ordered: walk it to the first chunk that reaches u
-        const int64_t vb = g.row[v], vend = g.row[v + 1];
-        for (int64_t e0 = vb; e0 < vend; e0 += 32) {
-          const int64_t e = e0 + lane;
-          const int32_t w = e < vend ? __ldg(g.col + e) : INT32_MAX;
-          const bool done = __any_sync(0xffffffffu, w >= u);
-          if (w < u) {
-            const int cw = colors[w];
-            if (cw != cu && cw != cv) {
-              atomicAdd(W2 + (int64_t)w * 8 + cv, 1u);
-              if (!(atomicOr(mark + w, 1u) & 1u)) L2[atomicAdd(&s_n2, 1)] = w;
-            }
-          }
-          if (done) break;
-        }
-      }
-      __syncthreads();
-      const int n2 = s_n2;
-      if (L >= 5) {
-        // level 3 pushed into the pair rows of the meeting vertices x
-        for (int i = wib; i < n2; i += NW) {
-          const int32_t w = L2[i];
-          const int cw = colors[w];
-          const uint4 r0 = *(const uint4 *)(W2 + (int64_t)w * 8);
-          const uint4 r1 = *(const uint4 *)(W2 + (int64_t)w * 8 + 4);
-          const uint32_t row[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-          const int64_t wb = g.row[w], wend = g.row[w + 1];
-          for (int64_t e0 = wb; e0 < wend; e0 += 32) {
+      // level 2: pairs (v, w), v in N<(u), w in N(v) below u; pass 0 claims w,
+      // pass 1 counts chi(v) into w's row.  v's row is rank ordered: it is
+      // walked to the first chunk that reaches u.
+      for (int pass = 0; pass < 2; pass++) {
+        for (int i = wib; i < du; i += NW) {
+          const int32_t v = __ldg(g.col + ub + i);
+          const int cv = colors[v];
+          if (cv == cu) continue;
+          const int64_t vb = g.row[v], vend = g.row[v + 1];
+          for (int64_t e0 = vb; e0 < vend; e0 += 32) {
             const int64_t e = e0 + lane;
-            const int32_t x = e < wend ? __ldg(g.col + e) : INT32_MAX;
-            const bool done = __any_sync(0xffffffffu, x >= u);
-            if (x < u) {
-              const int cx = colors[x];
-              if (cx != cu && cx != cw) {
-                bool any = false;
-#pragma unroll
-                for (int c = 0; c < 8; c++) {
-                  const uint32_t t = row[c];
-                  if (!t || c == cx) continue;
-                  atomicAdd(W3 + (int64_t)x * 16 + pair_idx(cw, c), t);
-                  any = true;
+            const int32_t w = e < vend ? __ldg(g.col + e) : INT32_MAX;
+            const bool done = __any_sync(FULL, w >= u);
+            if (w < u) {
+              const int cw = colors[w];
+              if (cw != cu && cw != cv) {
+                if (pass == 0) {
+                  if (atomicCAS(id2 + w, 0, -1) == 0) L2[atomicAdd(&s_n2, 1)] = w;
+                } else {
+                  atomicAdd(W2 + (int64_t)(id2[w] - 1) * 8 + cv, 1u);
                 }
-                if (any && !(atomicOr(mark + x, 2u) & 2u)) L3[atomicAdd(&s_n3, 1)] = x;
               }
             }
             if (done) break;
           }
         }
         __syncthreads();
+        if (pass == 0) {
+          for (int i = tid; i < s_n2; i += kPlThreads) id2[L2[i]] = i + 1;
+          __syncthreads();
+        }
       }
-      // closure at the meeting vertices
+      const int n2 = s_n2;
+      if (L >= 5) {
+        // level 3: pairs (w, x), w a level-2 vertex, x in N(w) below u; pass 0
+        // claims x, pass 1 adds w's row into x's pair row
+        for (int pass = 0; pass < 2; pass++) {
+          for (int i = wib; i < n2; i += NW) {
+            const int32_t w = L2[i];
+            const int cw = colors[w];
+            const uint4 r0 = *(const uint4 *)(W2 + (int64_t)i * 8);
+            const uint4 r1 = *(const uint4 *)(W2 + (int64_t)i * 8 + 4);
+            const uint32_t row[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            const int64_t wb = g.row[w], wend = g.row[w + 1];
+            for (int64_t e0 = wb; e0 < wend; e0 += 32) {
+              const int64_t e = e0 + lane;
+              const int32_t x = e < wend ? __ldg(g.col + e) : INT32_MAX;
+              const bool done = __any_sync(FULL, x >= u);
+              if (x < u) {
+                const int cx = colors[x];
+                if (cx != cu && cx != cw) {
+                  if (pass == 0) {
+                    bool any = false;
+#pragma unroll
+                    for (int c = 0; c < 8; c++) any = any || (row[c] != 0u && c != cx);
+                    if (any && atomicCAS(id3 + x, 0, -1) == 0) L3[atomicAdd(&s_n3, 1)] = x;
+                  } else {
+                    uint32_t *dst = W3 + (int64_t)(id3[x] - 1) * 16;
+#pragma unroll
+                    for (int c = 0; c < 8; c++) {
+                      const uint32_t t = row[c];
+                      if (t && c != cx) atomicAdd(dst + pair_idx(cw, c), t);
+                    }
+                  }
+                }
+              }
+              if (done) break;
+            }
+          }
+          __syncthreads();
+          if (pass == 0) {
+            for (int i = tid; i < s_n3; i += kPlThreads) id3[L3[i]] = i + 1;
+            __syncthreads();
+          }
+        }
+      }
+      // closure at the meeting vertices (level 3 for L >= 5, level 2 for L = 4)
       const int nx = L >= 5 ? s_n3 : n2;
-      const int32_t *LX = L >= 5 ? L3 : L2;
       u64 mine = 0;
       for (int i = tid; i < nx; i += kPlThreads) {
-        const int32_t x = LX[i];
-        if (L >= 5) L3[i] = 0;  // lists are cleared as they are consumed
+        const int32_t x = L >= 5 ? L3[i] : L2[i];
         const int cx = colors[x];
         const uint32_t fm = ((1u << k) - 1u) & ~((1u << cu) | (1u << cx));
         int f[4];
@@ -670,26 +696,25 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
           rest &= rest - 1;
         }
         if (L == 4) {
-          const u64 a0 = W2[(int64_t)x * 8 + f[0]], a1 = W2[(int64_t)x * 8 + f[1]];
+          const uint32_t *w2 = W2 + (int64_t)i * 8;
+          const u64 a0 = w2[f[0]], a1 = w2[f[1]];
           mine = add_ck(mine, mul_ck(2ull, mul_ck(a0, a1, ovf), ovf), ovf);
         } else if (L == 5) {
-          const uint32_t *w3 = W3 + (int64_t)x * 16;
-          const uint32_t *w2 = W2 + (int64_t)x * 8;
-          u64 t = mul_ck((u64)w2[f[0]], (u64)w3[pair_idx(f[1], f[2])], ovf);
-          t = add_ck(t, mul_ck((u64)w2[f[1]], (u64)w3[pair_idx(f[0], f[2])], ovf), ovf);
-          t = add_ck(t, mul_ck((u64)w2[f[2]], (u64)w3[pair_idx(f[0], f[1])], ovf), ovf);
-          mine = add_ck(mine, t, ovf);
+          const uint32_t *w3 = W3 + (int64_t)i * 16;
+          const int ix = id2[x];  // x's level-2 row (paths u-v-x), if x was reached at level 2
+          if (ix > 0) {
+            const uint32_t *w2 = W2 + (int64_t)(ix - 1) * 8;
+            u64 t = mul_ck((u64)w2[f[0]], (u64)w3[pair_idx(f[1], f[2])], ovf);
+            t = add_ck(t, mul_ck((u64)w2[f[1]], (u64)w3[pair_idx(f[0], f[2])], ovf), ovf);
+            t = add_ck(t, mul_ck((u64)w2[f[2]], (u64)w3[pair_idx(f[0], f[1])], ovf), ovf);
+            mine = add_ck(mine, t, ovf);
+          }
         } else {
-          const uint32_t *w3 = W3 + (int64_t)x * 16;
+          const uint32_t *w3 = W3 + (int64_t)i * 16;
           u64 t = mul_ck((u64)w3[pair_idx(f[0], f[1])], (u64)w3[pair_idx(f[2], f[3])], ovf);
           t = add_ck(t, mul_ck((u64)w3[pair_idx(f[0], f[2])], (u64)w3[pair_idx(f[1], f[3])], ovf), ovf);
           t = add_ck(t, mul_ck((u64)w3[pair_idx(f[0], f[3])], (u64)w3[pair_idx(f[1], f[2])], ovf), ovf);
           mine = add_ck(mine, mul_ck(2ull, t, ovf), ovf);
-        }
-        if (L >= 5) {
-          uint4 *z = (uint4 *)(W3 + (int64_t)x * 16);
-          z[0] = z[1] = z[2] = z[3] = make_uint4(0, 0, 0, 0);
-          atomicAnd(mark + x, ~2u);
         }
       }
       mine = warp_sum_ck(mine, ovf);
@@ -698,12 +723,20 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
         if (old + mine < old) ovf = 1;
       }
       __syncthreads();
+      // everything back to zero: rows by local index, ids through the lists
+      if (L >= 5) {
+        for (int i = tid; i < s_n3; i += kPlThreads) {
+          id3[L3[i]] = 0;
+          L3[i] = 0;
+          uint4 *z = (uint4 *)(W3 + (int64_t)i * 16);
+          z[0] = z[1] = z[2] = z[3] = make_uint4(0, 0, 0, 0);
+        }
+      }
       for (int i = tid; i < n2; i += kPlThreads) {
-        const int32_t w = L2[i];
+        id2[L2[i]] = 0;
         L2[i] = 0;
-        uint4 *z = (uint4 *)(W2 + (int64_t)w * 8);
+        uint4 *z = (uint4 *)(W2 + (int64_t)i * 8);
         z[0] = z[1] = make_uint4(0, 0, 0, 0);
-        atomicAnd(mark + w, ~1u);
       }
     }
     if (ovf) atomicOr(&s_ovf, 1u);
@@ -748,6 +781,7 @@ int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank) {
   S.o_w2 = take((size_t)n * 32);
   S.o_w3 = a.L >= 5 ? take((size_t)n * 64) : 0;
   S.o_mark = take((size_t)n * 4);
+  S.o_id3 = a.L >= 5 ? take((size_t)n * 4) : 0;
   S.o_l2 = take((size_t)n * 4);
   S.o_l3 = a.L >= 5 ? take((size_t)n * 4) : 0;
   S.slot_bytes = off;

@@ -86,6 +86,7 @@ extern "C" int cc_count_cycle_noalloc(int device, void *cuda_stream, int L, int6
   S.o_w2 = take((size_t)n * 32);
   S.o_w3 = L >= 5 ? take((size_t)n * 64) : 0;
   S.o_mark = take((size_t)n * 4);
+  S.o_id3 = L >= 5 ? take((size_t)n * 4) : 0;
   S.o_l2 = take((size_t)n * 4);
   S.o_l3 = L >= 5 ? take((size_t)n * 4) : 0;
   S.slot_bytes = off;
