@@ -662,11 +662,11 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
                     for (int c = 0; c < 8; c++) any = any || (row[c] != 0u && c != cx);
                     if (any && atomicCAS(id3 + x, 0, -1) == 0) L3[atomicAdd(&s_n3, 1)] = x;
                   } else {
-                    uint32_t *dst = W3 + (int64_t)(id3[x] - 1) * 16;
+                    const int ix = id3[x];  // numbered in pass 0 whenever a row entry below applies
 #pragma unroll
                     for (int c = 0; c < 8; c++) {
                       const uint32_t t = row[c];
-                      if (t && c != cx) atomicAdd(dst + pair_idx(cw, c), t);
+                      if (t && c != cx) atomicAdd(W3 + (int64_t)(ix - 1) * 16 + pair_idx(cw, c), t);
                     }
                   }
                 }
