@@ -35,7 +35,6 @@ namespace cc {
 
 constexpr int kMaxPartial = 128;
 constexpr int kHubDegree = 32;        // sources of at least this degree take the CTA kernel
-constexpr int kHubBigDegree = 1024;   // ... and from this degree on, a launch with large hash tables
 constexpr int kHubMaxSlots = 16384;   // hash slots per CTA (N<(u) of up to 8192 vertices)
 constexpr int kHubThreads = 256;
 
@@ -303,14 +302,14 @@ __global__ void __launch_bounds__(256) k_triangle(TriArgs a, TriMode md, int32_t
 
 __device__ __forceinline__ uint32_t hub_hash(int32_t w) { return (uint32_t)w * 0x9E3779B1u; }
 
-// One CTA per source u in [u_lo, u_hi), highest first.  Shared memory:
+// One CTA per source u in [u_lo, n), highest first.  Shared memory:
 //   acc[R_acc]        u's output row (unary output only), all zero between sources
 //   keys[max_slots]   hash set of N<(u) (-1 = empty), all empty between sources
 //   kpos[max_slots]   index of the key in N<(u) (only when positions are needed)
 // A source with |N<(u)| > max_slots / 2 scans by binary search instead.
 template <int kForm>
-__global__ void __launch_bounds__(kHubThreads) k_triangle_hub(TriArgs a, TriMode md, int32_t u_lo, int32_t u_hi,
-                                                              int max_slots, int R_acc) {
+__global__ void __launch_bounds__(kHubThreads) k_triangle_hub(TriArgs a, TriMode md, int32_t u_lo, int max_slots,
+                                                              int R_acc) {
   extern __shared__ __align__(16) unsigned char smem[];
   u64 *acc = reinterpret_cast<u64 *>(smem);
   int32_t *keys = reinterpret_cast<int32_t *>(smem + (size_t)R_acc * 8);
@@ -322,14 +321,14 @@ __global__ void __launch_bounds__(kHubThreads) k_triangle_hub(TriArgs a, TriMode
   for (int i = tid; i < max_slots; i += blockDim.x) keys[i] = -1;
   for (int i = tid; i < R_acc; i += blockDim.x) acc[i] = 0;
   if (tid == 0) s_root = 0;
-  const int32_t n_hub = u_hi - u_lo;
+  const int32_t n_hub = (int32_t)(a.g.n - u_lo);
   while (true) {
     __syncthreads();  // readers of s_idx and the previous source's clean-up are done
     if (tid == 0) s_idx = atomicAdd(a.work_counter, 1);
     __syncthreads();
     const int idx = s_idx;
     if (idx >= n_hub) break;
-    const int32_t u = u_hi - 1 - idx;
+    const int32_t u = (int32_t)(a.g.n - 1 - idx);
     const int64_t ub = a.g.row[u];
     const int du = a.g.lo_cnt[u];
     if (du < 2) continue;
@@ -416,51 +415,41 @@ __global__ void __launch_bounds__(kHubThreads) k_triangle_hub(TriArgs a, TriMode
   if (ovf & 2u) atomicOr(a.status + ST_TIMEOUT, 2ull);  // partial list capacity exceeded
 }
 
-// One launch of the CTA kernel over ranks [u_lo, u_hi), its hash tables
-// sized for the largest degree there (shared memory bounds the CTAs per SM).
-template <int kForm>
-static int launch_hub_range(Ctx &c, const TriArgs &a, const TriMode &md, int32_t u_lo, int32_t u_hi) {
-  if (u_lo >= u_hi) return CC_OK;
-  const int64_t max_deg = c.cur_graph_row[u_hi] - c.cur_graph_row[u_hi - 1];
-  int max_slots = 64;
-  while (max_slots < kHubMaxSlots && max_slots < 2 * max_deg) max_slots <<= 1;
-  const int R_acc = a.nb == 1 ? ((a.R_out + 1) & ~1) : 0;
-  const size_t smem = (size_t)R_acc * 8 + (size_t)max_slots * (md.need_pos ? 6 : 4);
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k_triangle_hub<kForm>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return CC_ERR_CUDA;
-  int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triangle_hub<kForm>, kHubThreads, smem) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess)
-    return CC_ERR_CUDA;
-  const int64_t grid = std::min<int64_t>((int64_t)std::max(per_sm, 1) * sms, u_hi - u_lo);
-  if (cudaMemsetAsync(a.work_counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
-  k_triangle_hub<kForm><<<(int)grid, kHubThreads, smem, c.stream>>>(a, md, u_lo, u_hi, max_slots, R_acc);
-  c.kernels++;
-  return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
-}
-
 template <int kForm>
 int launch_triangle_form(Ctx &c, const TriArgs &a, const TriMode &md, const char *name) {
+  // sources of degree >= kHubDegree: ranks [u_lo, n) (degree grows with rank)
   const int64_t n = a.g.n;
-  // first rank of degree >= d (degree grows with rank)
-  auto first_of_degree = [&](int64_t d) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-      int64_t mid = (lo + hi) / 2;
-      if (c.cur_graph_row[mid + 1] - c.cur_graph_row[mid] >= d) hi = mid;
-      else lo = mid + 1;
-    }
-    return (int32_t)lo;
-  };
-  const int32_t u_lo = first_of_degree(kHubDegree);
-  // hubs of degree >= kHubBigDegree get their large tables in a launch of their
-  // own, so the many smaller hubs run more CTAs per SM
-  const int32_t u_big = std::max(u_lo, first_of_degree(kHubBigDegree));
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) / 2;
+    if (c.cur_graph_row[mid + 1] - c.cur_graph_row[mid] >= kHubDegree) hi = mid;
+    else lo = mid + 1;
+  }
+  const int32_t u_lo = (int32_t)lo;
+  int max_slots = 64, R_acc = 0;
+  size_t smem = 0;
+  int64_t grid = 0;
+  if (u_lo < n) {
+    const int64_t max_deg = c.cur_graph_row[n] - c.cur_graph_row[n - 1];
+    while (max_slots < kHubMaxSlots && max_slots < 2 * max_deg) max_slots <<= 1;
+    R_acc = a.nb == 1 ? ((a.R_out + 1) & ~1) : 0;
+    smem = (size_t)R_acc * 8 + (size_t)max_slots * (md.need_pos ? 6 : 4);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_triangle_hub<kForm>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return CC_ERR_CUDA;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triangle_hub<kForm>, kHubThreads, smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess)
+      return CC_ERR_CUDA;
+    grid = std::min<int64_t>((int64_t)std::max(per_sm, 1) * sms, n - u_lo);
+  }
   timing_begin(c, name);
-  int rc = launch_hub_range<kForm>(c, a, md, u_big, (int32_t)n);
-  if (rc == CC_OK) rc = launch_hub_range<kForm>(c, a, md, u_lo, u_big);
-  if (rc != CC_OK) return rc;
+  if (u_lo < n) {
+    if (cudaMemsetAsync(a.work_counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
+    k_triangle_hub<kForm><<<(int)grid, kHubThreads, smem, c.stream>>>(a, md, u_lo, max_slots, R_acc);
+    c.kernels++;
+    if (cudaGetLastError() != cudaSuccess) return CC_ERR_CUDA;
+  }
   if (u_lo > 0) {
     if (cudaMemsetAsync(a.work_counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
     k_triangle<kForm><<<152 * 8, 256, 0, c.stream>>>(a, md, u_lo);
