@@ -206,7 +206,24 @@ extern "C" int cc_autotune(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int 
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    for (int hd = 64; hd <= 4096; hd *= 2) {
+    // thresholds 64 .. 4096 in steps of 1.5 and 4/3; one untimed run first
+    // takes the one-time costs (scratch allocation, per-graph tables)
+    static const int kCandidates[] = {64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096};
+    {
+      u64 cnt = 0;
+      bool ovf = false;
+      c.heavy_degree = 256;
+      int rc = run_plan(c, g, p, 0, &cnt, &ovf, nullptr, nullptr);
+      if (rc == CC_OK && cudaStreamSynchronize(c.stream) != cudaSuccess) rc = CC_ERR_CUDA;
+      if (rc != CC_OK) {
+        c.heavy_degree = saved;
+        c.timing = timing;
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return rc;
+      }
+    }
+    for (int hd : kCandidates) {
       if (hd > 2 * g.max_deg && !first) break;
       c.heavy_degree = hd;
       u64 cnt = 0;
