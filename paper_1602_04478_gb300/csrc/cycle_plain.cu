@@ -153,66 +153,95 @@ __device__ __forceinline__ void pc_count(uint32_t (&cnt)[L], int c, uint32_t v) 
   }
 }
 
-template <int L>
-__global__ void __launch_bounds__(kPcThreads) k_pc_levels_pull(GraphView g, const uint8_t *colors, PcScratch S,
-                                                               PcGroup G) {
+// NG = 1: one group (bank A); NG = 2: groups A and B, each writing its own
+// bank, in one pass over the vertices w (the scan of N(w) is shared).
+template <int L, int NG>
+__global__ void __launch_bounds__(kPcThreads) k_pc_levels_pull(GraphView g, const uint8_t *colors, PcScratch SA,
+                                                               PcGroup GA, PcScratch SB, PcGroup GB) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, b = lane;
-  const bool active = b < G.B;
-  const int32_t ub = active ? G.u[b] : -1;
-  const int cu = active ? colors[ub] : -1;
-  const int32_t umax = G.umax;
+  bool active[NG];
+  int32_t ub[NG];
+  int cu[NG];
   // member[v] as two 32-bit halves: [2v] level-1 bits (read here), [2v+1]
   // level-2 bits (written here)
-  uint32_t *half = reinterpret_cast<uint32_t *>(S.member);
+  uint32_t *half[NG];
+#pragma unroll
+  for (int q = 0; q < NG; q++) {
+    const PcGroup &G = q == 0 ? GA : GB;
+    active[q] = b < G.B;
+    ub[q] = active[q] ? G.u[b] : -1;
+    cu[q] = active[q] ? colors[ub[q]] : -1;
+    half[q] = reinterpret_cast<uint32_t *>(q == 0 ? SA.member : SB.member);
+  }
+  const int32_t umax = GA.umax;
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t wi = warp0; wi < umax; wi += nwarps) {
     const int32_t w = (int32_t)wi;
     const int cw = colors[w];
-    const bool act = active && w < ub && cw != cu;
-    uint32_t cnt[L];
+    bool act[NG];
+    bool any_act = false;
+    uint32_t cnt[NG][L];
 #pragma unroll
-    for (int c = 0; c < L; c++) cnt[c] = 0;
-    if (__any_sync(FULL, act)) {
+    for (int q = 0; q < NG; q++) {
+      act[q] = active[q] && w < ub[q] && cw != cu[q];
+      any_act = any_act || act[q];
+#pragma unroll
+      for (int c = 0; c < L; c++) cnt[q][c] = 0;
+    }
+    if (__any_sync(FULL, any_act)) {
       const int64_t wb = g.row[w];
       const int deg = (int)(g.row[w + 1] - wb);
       for (int base = 0; base < deg; base += 32) {
         const int j = base + lane;
         const int32_t vl = j < deg ? __ldg(g.col + wb + j) : INT32_MAX;
         const bool past = __any_sync(FULL, vl >= umax);
-        uint32_t ml = vl < umax ? __ldcg(half + 2 * (int64_t)vl) : 0u;
-        const int cl = ml ? colors[vl] : cw;
-        if (cl == cw) ml = 0u;  // chi(v) = chi(w): no colourful path u-v-w
-        unsigned m = __ballot_sync(FULL, ml != 0u);
+        uint32_t ml[NG];
+        uint32_t mor = 0u;
+#pragma unroll
+        for (int q = 0; q < NG; q++) {
+          ml[q] = vl < umax ? __ldcg(half[q] + 2 * (int64_t)vl) : 0u;
+          mor |= ml[q];
+        }
+        const int cl = mor ? colors[vl] : cw;
+        // chi(v) = chi(w): no colourful path u-v-w
+        unsigned m = __ballot_sync(FULL, mor != 0u && cl != cw);
         while (m) {
 #pragma unroll
-          for (int q = 0; q < 4; q++) {
+          for (int r = 0; r < 4; r++) {
             const int t = m ? __ffs(m) - 1 : 0;
             const bool valid = m != 0u;
             m &= m - 1u;
-            const uint32_t mm = __shfl_sync(FULL, ml, t);
             const int cc = __shfl_sync(FULL, cl, t);
-            if (valid) pc_count<L>(cnt, cc, (act && ((mm >> b) & 1u)) ? 1u : 0u);
+#pragma unroll
+            for (int q = 0; q < NG; q++) {
+              const uint32_t mm = __shfl_sync(FULL, ml[q], t);
+              if (valid) pc_count<L>(cnt[q], cc, (act[q] && ((mm >> b) & 1u)) ? 1u : 0u);
+            }
           }
         }
         if (past) break;
       }
     }
-    bool nz = false;
+    bool nz_any = false;
 #pragma unroll
-    for (int c = 0; c < L; c++) nz = nz || cnt[c] != 0u;
-    if (nz) {
-      uint32_t wd[4] = {0u, 0u, 0u, 0u};
+    for (int q = 0; q < NG; q++) {
+      const PcScratch &S = q == 0 ? SA : SB;
+      bool nz = false;
 #pragma unroll
-      for (int c = 0; c < L; c++) wd[c >> 1] |= cnt[c] << (16 * (c & 1));
-      *(uint4 *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+      for (int c = 0; c < L; c++) nz = nz || cnt[q][c] != 0u;
+      if (nz) {
+        uint32_t wd[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int c = 0; c < L; c++) wd[c >> 1] |= cnt[q][c] << (16 * (c & 1));
+        *(uint4 *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+      }
+      const unsigned bits = __ballot_sync(FULL, nz);
+      if (lane == 0) half[q][2 * (int64_t)w + 1] = bits;
+      nz_any = nz_any || bits != 0u;
     }
-    const unsigned bits = __ballot_sync(FULL, nz);
-    if (lane == 0) {
-      half[2 * (int64_t)w + 1] = bits;
-      if (bits) atomicOr(S.anym + (w >> 5), 1u << (w & 31));
-    }
+    if (lane == 0 && nz_any) atomicOr(SA.anym + (w >> 5), 1u << (w & 31));
   }
 }
 
@@ -876,10 +905,16 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
     int rc = push_work(c, a.g, &pw);
     if (rc != CC_OK) return rc;
   }
-  // groups of the pull-form level build use bank 0 and leave it to be zeroed
+  // groups of the pull-form level build leave their banks to be zeroed
+  bool pulled_b1 = false;  // bank 1 served a pull-form group
   auto zero_levels = [&]() {
-    return cudaMemsetAsync(S0.member, 0, (size_t)n * 8, c.stream) == cudaSuccess &&
-           cudaMemsetAsync(S0.w2, 0, (size_t)kPcMaxB * n * 16, c.stream) == cudaSuccess;
+    for (int q = 0; q < (pulled_b1 ? 2 : 1); q++) {
+      const PcScratch &S = q == 0 ? S0 : S1;
+      if (cudaMemsetAsync(S.member, 0, (size_t)n * 8, c.stream) != cudaSuccess ||
+          cudaMemsetAsync(S.w2, 0, (size_t)kPcMaxB * n * 16, c.stream) != cudaSuccess)
+        return false;
+    }
+    return true;
   };
   auto group_at = [&](int64_t top) {
     PcGroup G;
@@ -918,21 +953,41 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
     // the one-bit member map is rebuilt for every pass
     if (cudaMemsetAsync(S0.anym, 0, anym_bytes, c.stream) != cudaSuccess) return CC_ERR_CUDA;
     if (use_pull) {
-      const int64_t du = c.cur_graph_row[top + 1] - c.cur_graph_row[top];
+      // pull form, two groups per pass when the next one qualifies too
+      bool two = false;
+      PcGroup G2 = G;
+      if (top - kPcMaxB >= first_rank) {
+        G2 = group_at(top - kPcMaxB);
+        double work = 0;
+        for (int b = 0; b < G2.B; b++) work += (double)pw[G2.u[b]];
+        two = work > kPullLevelsRatio * (double)c.cur_graph_row[G2.umax];
+      }
       timing_begin(c, "cycle_plain_levels_pull");
-      dim3 gm((unsigned)std::max<int64_t>(1, std::min<int64_t>(sms, (du + kPcThreads - 1) / kPcThreads)), G.B);
-      k_pc_mark1<<<gm, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G, L <= 5);
-      c.kernels++;
-      k_pc_levels_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G);
+      for (int q = 0; q < (two ? 2 : 1); q++) {
+        const PcGroup &Gq = q == 0 ? G : G2;
+        const int64_t du = c.cur_graph_row[Gq.umax + 1] - c.cur_graph_row[Gq.umax];
+        dim3 gm((unsigned)std::max<int64_t>(1, std::min<int64_t>(sms, (du + kPcThreads - 1) / kPcThreads)), Gq.B);
+        k_pc_mark1<<<gm, kPcThreads, 0, c.stream>>>(a.g, a.colors, q == 0 ? S0 : S1, Gq, L <= 5);
+        c.kernels++;
+      }
+      if (two)
+        k_pc_levels_pull<L, 2><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G, S1, G2);
+      else
+        k_pc_levels_pull<L, 1><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G, S0, G);
       c.kernels++;
       timing_end(c);
       timing_begin(c, "cycle_plain_pull");
-      k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S0, G, a.colors, a.status);
+      if (two)
+        k_pc_pull2<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S0, G, S1, G2, a.colors, a.status);
+      else
+        k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S0, G, a.colors, a.status);
       c.kernels++;
       timing_end(c);
       close_group(S0, G);
+      if (two) close_group(S1, G2);
       pulled = true;
-      top -= kPcMaxB;
+      pulled_b1 = pulled_b1 || two;
+      top -= two ? 2 * kPcMaxB : kPcMaxB;
       continue;
     }
     // push form: two groups per pass when two remain
