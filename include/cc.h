@@ -167,8 +167,9 @@ int cc_count_batch(cc_ctx *ctx, const cc_request *reqs, int n_reqs, uint64_t *co
 /* Whether cc_count_batch records and replays CUDA graphs (default 1). */
 int cc_set_graph_capture(cc_ctx *ctx, int enable);
 /* Time the root-cycle closure of query_id on graph_id for heavy-source
- * degree thresholds 64, 128, ..., 4096 (up to twice the maximum degree) on
- * one colouring and keep the fastest for this (graph, query); later counts
+ * degree thresholds 64, 96, 128, 192, ..., 3072, 4096 (steps of 1.5 and 4/3,
+ * up to twice the maximum degree) on one colouring, after one untimed run,
+ * and keep the fastest for this (graph, query); later counts
  * use it unless cc_set_heavy_degree forces a value.  *heavy_degree
  * (nullable) receives the choice. */
 int cc_autotune(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int *heavy_degree);

@@ -438,7 +438,8 @@ def test_autotune_keeps_counts(cc):
         qid = cc.set_query(*QUERIES["C6"])
         before = [int(x) for x in cc.count(gid, qid, 0, 2)[0]]
         hd = P.cc_autotune(cc.h, gid, qid)
-        assert hd in (64, 128, 256, 512, 1024, 2048, 4096)
+        # the tuner's candidate thresholds
+        assert hd in (64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096)
         assert [int(x) for x in cc.count(gid, qid, 0, 2)[0]] == before
         res, _ = P.cc_count_batch(cc.h, [(gid, qid, 0, 2)])
         assert [int(x) for x in res[0]] == before
