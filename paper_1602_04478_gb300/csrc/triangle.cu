@@ -355,39 +355,14 @@ __global__ void __launch_bounds__(kHubThreads) k_triangle_hub(TriArgs a, TriMode
     USink sk;
     if (a.nb == 1) sk.u = u, sk.acc = acc;
     u64 root_acc = 0, units = 0;
-    // wedges (v, w) of u, load-balanced: a warp takes 32 lower neighbours v
-    // at a time (one per lane), prefix-sums their lists' lengths and hands
-    // out the wedges 32 per step, each lane finding its v among the prefix
-    for (int i0 = 1 + 32 * warp; i0 < du; i0 += 32 * nwarps) {
-      const int ivl = i0 + lane;
-      const bool valid = ivl < du;
-      const int32_t vl = valid ? __ldg(a.g.col + ub + ivl) : 0;
-      const int dvl = valid ? a.g.lo_cnt[vl] : 0;
-      units += (u64)dvl;
-      const int cvl = valid ? a.colors[vl] : cu;
-      const int de = cvl == cu ? 0 : dvl;  // chi(v) = chi(u) closes no colourful triangle
-      const int64_t vbl = de ? a.g.row[vl] : 0;
-      int pre = de;  // inclusive prefix over the lanes
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, pre, o);
-        if (lane >= o) pre += t;
-      }
-      const int total = __shfl_sync(0xffffffffu, pre, 31);
-      for (int f0 = 0; f0 < total; f0 += 32) {
-        const int f = f0 + lane;
-        // owner lane: the first whose inclusive prefix exceeds f
-        int o = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1)
-          if (__shfl_sync(0xffffffffu, pre, o + step - 1) <= f) o += step;
-        const int pre_o = __shfl_sync(0xffffffffu, pre, o), de_o = __shfl_sync(0xffffffffu, de, o);
-        const int32_t v = __shfl_sync(0xffffffffu, vl, o);
-        const int cv = __shfl_sync(0xffffffffu, cvl, o);
-        const int iv = __shfl_sync(0xffffffffu, ivl, o);
-        const int64_t vb = __shfl_sync(0xffffffffu, vbl, o);
-        if (f >= total) continue;
-        const int j = f - (pre_o - de_o);
+    for (int iv = 1 + warp; iv < du; iv += nwarps) {
+      const int32_t v = __ldg(a.g.col + ub + iv);
+      const int dv = a.g.lo_cnt[v];
+      units += (u64)dv;
+      const int cv = a.colors[v];
+      if (cv == cu) continue;
+      const int64_t vb = a.g.row[v];
+      for (int j = lane; j < dv; j += 32) {
         const int32_t w = __ldg(a.g.col + vb + j);
         int64_t p = -1;
         if (hashed) {
@@ -410,11 +385,7 @@ __global__ void __launch_bounds__(kHubThreads) k_triangle_hub(TriArgs a, TriMode
         tri_visit<kForm>(a, md, sk, u, v, w, cu, cv, cw, ub + iv, p, vb + j, root_acc, ovf);
       }
     }
-    if (a.count_units) {
-      unsigned uo = 0;
-      units = warp_sum_ck(units, uo);
-      if (lane == 0 && units) atomicAdd(a.status + ST_UNITS, units);
-    }
+    if (a.count_units && lane == 0 && units) atomicAdd(a.status + ST_UNITS, units);
     if (a.nb == 0) {
       root_acc = warp_sum_ck(root_acc, ovf);
       if (lane == 0 && root_acc) atomic_add_ck(&s_root, root_acc, ovf);
