@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const ui
 // member map -- is paid once for 64 sources; each group is then visited and
 // closed as in k_pc_pull (lane b = source b of A, then of B).
 template <int L>
-__global__ void __launch_bounds__(kPcThreads, 3) k_pc_pull2(GraphView g, const uint32_t *tag, PcScratch SA, PcGroup GA,
+__global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull2(GraphView g, const uint32_t *tag, PcScratch SA, PcGroup GA,
                                                          PcScratch SB, PcGroup GB, const uint8_t *colors,
                                                          u64 *status) {
   constexpr int NP = L * (L - 1) / 2;
@@ -1003,7 +1003,7 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
     timing_end(c);
     timing_begin(c, "cycle_plain_pull");
     if (two)
-      k_pc_pull2<L><<<sms * 3, kPcThreads, 0, c.stream>>>(a.g, tag, S0, G, S1, G2, a.colors, a.status);
+      k_pc_pull2<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S0, G, S1, G2, a.colors, a.status);
     else
       k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S0, G, a.colors, a.status);
     c.kernels++;
