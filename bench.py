@@ -449,7 +449,33 @@ def main():
         barrier()
         p3 = time.perf_counter() - t0
         equal = all([int(x) for x in res3[i][:Tp]] == plain3[name] for i, name in enumerate(q3))
+        # the same comparison on a small graph (n = 1e4), where a colouring is
+        # ~1 ms of kernels and per-call overhead is what batching removes
+        gs = gg.chung_lu(10_000, 8, 2.1, 3)
+        gid_s = ctx.load_graph(gs)
+        reqs_s = [(gid_s, q, first3, T3) for q in q3.values()]
+        P.cc_count_batch(ctx.h, reqs_s)  # eager run + capture (untimed)
+        barrier()
+        t0 = time.perf_counter()
+        res_s, _ = P.cc_count_batch(ctx.h, reqs_s)
+        barrier()
+        bs = time.perf_counter() - t0
+        plain_s = {}
+        barrier()
+        t0 = time.perf_counter()
+        for name, q in q3.items():
+            plain_s[name] = [int(ctx.count(gid_s, q, first3 + t, 1)[0][0]) for t in range(T3)]
+        barrier()
+        ps = time.perf_counter() - t0
+        equal_s = all([int(x) for x in res_s[i]] == plain_s[name] for i, name in enumerate(q3))
+        ctx.free_graph(gid_s)
+        batch_cfg_small = {"workload": f"chung_lu n=10000 mean_deg=8 gamma=2.1 seed=3; {T3} colourings x "
+                                       f"{len(q3)} queries per cc_count_batch call",
+                           "colorings_per_s_batched": len(q3) * T3 * world / bs,
+                           "colorings_per_s_plain": len(q3) * T3 * world / ps,
+                           "counts_equal_batched_vs_plain": bool(equal_s)}
         batch_cfg = {"workload": f"{workload_name()}; {T3} colourings x {len(q3)} queries per cc_count_batch call",
+                     "small_graph": batch_cfg_small,
                      "queries": list(q3), "trials": T3,
                      "colorings_per_s_batched": len(q3) * T3 * world / b3,
                      "colorings_per_s_plain": len(q3) * Tp * world / p3,
