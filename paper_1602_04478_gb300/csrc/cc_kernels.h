@@ -87,17 +87,12 @@ bool plain_cycle_eligible(const CycleArgs &a);
 int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank);
 int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank);
 
-// scratch slots of the per-CTA plain-cycle push kernel (one slot per CTA):
-// rows by local index, per-level hash tables vertex -> local index (entries
-// {vertex + 1, index + 1}, 2^tab_bits of them), lists local index -> table slot
+// scratch slots of the per-CTA plain-cycle push kernel (one slot per CTA)
 struct PlScratch {
   char *base;
   size_t slot_bytes;
-  size_t o_rows2, o_rows3, o_tab2, o_tab3, o_list2, o_list3;
-  int tab_bits;
+  size_t o_w2, o_w3, o_mark, o_id3, o_l2, o_l3;  // rows by local index; ids by vertex; lists
 };
-// fills the offsets for n vertices and an L-cycle; returns the slot size
-size_t pl_layout(PlScratch &S, int64_t n, int L);
 int launch_pc_light_raw(cudaStream_t stream, int L, const GraphView &g, const uint8_t *colors, const PlScratch &S,
                         int slots, int32_t end_rank, int *work, u64 *status, int k);
 int heavy_group_size(const CycleArgs &a);

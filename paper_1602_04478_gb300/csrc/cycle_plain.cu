@@ -589,56 +589,16 @@ __global__ void k_pc_finish(PcScratch S, PcGroup G, int multiplier, u64 *per_ver
 // deg(x) * deg(u), which the host checks stays below 2^32.
 //
 // The rows of one source are compact: a vertex reached at level 2 (3) gets
-// the next local index, and its row lives at that index.  Vertices are found
-// through a per-level open-addressing hash table of the slot, used only up to
-// a size fitted to a bound on the level's reach (twice the bound, rounded up
-// to a power of two), so a source's tables and rows stay small and in cache.
-// Each level is walked twice: the first walk claims the vertices (a table
-// entry, whose slot goes on the level's list), the CTA then numbers the list,
-// and the second walk finds each vertex's number and adds into its row.
+// the next local index, and its row lives at that index, so the rows a source
+// touches are contiguous and stay in cache.  Each level is walked twice: the
+// first walk claims the vertices (id[v] = -1 marks a claim, the claimant
+// lists it), the CTA then numbers the list (id[v] = index + 1), and the second
+// walk adds into the numbered rows.
 constexpr int kPlThreads = 256;
 
 __device__ __forceinline__ int pair_idx(int a, int b) {
   int hi = a > b ? a : b, lo = a > b ? b : a;
   return hi * (hi - 1) / 2 + lo;
-}
-
-__device__ __forceinline__ uint32_t pl_hash(int32_t v, int bits) { return ((uint32_t)v * 0x9E3779B1u) >> (32 - bits); }
-
-// Claim v in table t (2^bits entries, at most half full): the slot when this
-// thread inserted v, -1 when v was there already.
-__device__ __forceinline__ int pl_claim(uint2 *t, int bits, int32_t v) {
-  const uint32_t mask = (1u << bits) - 1u, key = (uint32_t)v + 1u;
-  uint32_t h = pl_hash(v, bits);
-  for (uint32_t probe = 0; probe <= mask; probe++, h = (h + 1u) & mask) {
-    const uint32_t k = __ldcg(&t[h].x);
-    if (k == key) return -1;
-    if (k == 0u) {
-      const uint32_t old = atomicCAS(&t[h].x, 0u, key);
-      if (old == 0u) return (int)h;
-      if (old == key) return -1;
-    }
-  }
-  return -1;  // not reached: the table is never more than half full
-}
-
-// Local index + 1 of v in table t, 0 when absent.
-__device__ __forceinline__ int pl_find(const uint2 *t, int bits, int32_t v) {
-  const uint32_t mask = (1u << bits) - 1u, key = (uint32_t)v + 1u;
-  uint32_t h = pl_hash(v, bits);
-  for (uint32_t probe = 0; probe <= mask; probe++, h = (h + 1u) & mask) {
-    const uint2 e = __ldcg(&t[h]);
-    if (e.x == key) return (int)e.y;
-    if (e.x == 0u) return 0;
-  }
-  return 0;
-}
-
-// log2 of the table size for a level reaching at most `bound` vertices
-__device__ __forceinline__ int pl_bits(unsigned long long bound, int max_bits) {
-  int bits = 6;
-  while (bits < max_bits && (1ull << bits) < 2ull * bound) bits++;
-  return bits;
 }
 
 template <int L>
@@ -647,18 +607,17 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
                                                          u64 *per_vertex, u64 *status, int k) {
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ int s_u, s_n2, s_n3;
-  __shared__ unsigned long long s_tot, s_bound;
+  __shared__ unsigned long long s_tot;
   __shared__ unsigned s_ovf;
   char *slot = S.base + (size_t)blockIdx.x * S.slot_bytes;
-  uint32_t *W2 = (uint32_t *)(slot + S.o_rows2);  // [local][8] level-2 rows by colour of v
-  uint32_t *W3 = (uint32_t *)(slot + S.o_rows3);  // [local][16] level-3 rows by colour pair
-  uint2 *T2 = (uint2 *)(slot + S.o_tab2);         // level-2 table
-  uint2 *T3 = (uint2 *)(slot + S.o_tab3);         // level-3 table
-  int32_t *L2 = (int32_t *)(slot + S.o_list2);    // local index -> table slot
-  int32_t *L3 = (int32_t *)(slot + S.o_list3);
+  uint32_t *W2 = (uint32_t *)(slot + S.o_w2);   // [local][8] level-2 rows by colour of v
+  uint32_t *W3 = (uint32_t *)(slot + S.o_w3);   // [local][16] level-3 rows by colour pair
+  int32_t *id2 = (int32_t *)(slot + S.o_mark);  // [n] local index + 1 at level 2 (0 none, -1 claimed)
+  int32_t *id3 = (int32_t *)(slot + S.o_id3);   // [n] the same at level 3
+  int32_t *L2 = (int32_t *)(slot + S.o_l2);     // local index -> vertex
+  int32_t *L3 = (int32_t *)(slot + S.o_l3);
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   constexpr int NW = kPlThreads / 32;
-  const int64_t n = g.n;
   while (true) {
     if (tid == 0) {
       s_u = end_rank - 1 - atomicAdd(work, 1);
@@ -666,7 +625,6 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
       s_n3 = 0;
       s_tot = 0;
       s_ovf = 0;
-      s_bound = 0;
     }
     __syncthreads();
     const int32_t u = s_u;
@@ -676,18 +634,6 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
     const int du = g.lo_cnt[u];
     unsigned ovf = 0;
     if (du >= 2) {
-      // level-2 reach is at most the summed degrees of u's lower neighbours
-      {
-        unsigned long long d = 0;
-        for (int i = tid; i < du; i += kPlThreads) {
-          const int32_t v = __ldg(g.col + ub + i);
-          d += (unsigned long long)(g.row[v + 1] - g.row[v]);
-        }
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULL, d, o);
-        if (lane == 0) atomicAdd(&s_bound, d);
-      }
-      __syncthreads();
-      const int bits2 = pl_bits(min((unsigned long long)n, s_bound), S.tab_bits);
       // level 2: pairs (v, w), v in N<(u), w in N(v) below u; pass 0 claims w,
       // pass 1 counts chi(v) into w's row.  v's row is rank ordered: it is
       // walked to the first chunk that reaches u.
@@ -705,10 +651,9 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
               const int cw = colors[w];
               if (cw != cu && cw != cv) {
                 if (pass == 0) {
-                  const int sl = pl_claim(T2, bits2, w);
-                  if (sl >= 0) L2[atomicAdd(&s_n2, 1)] = sl;
+                  if (atomicCAS(id2 + w, 0, -1) == 0) L2[atomicAdd(&s_n2, 1)] = w;
                 } else {
-                  atomicAdd(W2 + (int64_t)(pl_find(T2, bits2, w) - 1) * 8 + cv, 1u);
+                  atomicAdd(W2 + (int64_t)(id2[w] - 1) * 8 + cv, 1u);
                 }
               }
             }
@@ -717,31 +662,17 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
         }
         __syncthreads();
         if (pass == 0) {
-          for (int i = tid; i < s_n2; i += kPlThreads) T2[L2[i]].y = (uint32_t)(i + 1);
-          if (tid == 0) s_bound = 0;
+          for (int i = tid; i < s_n2; i += kPlThreads) id2[L2[i]] = i + 1;
           __syncthreads();
         }
       }
       const int n2 = s_n2;
-      int bits3 = 6;
       if (L >= 5) {
-        // level-3 reach is at most the summed degrees of the level-2 vertices
-        {
-          unsigned long long d = 0;
-          for (int i = tid; i < n2; i += kPlThreads) {
-            const int32_t w = (int32_t)(T2[L2[i]].x - 1u);
-            d += (unsigned long long)(g.row[w + 1] - g.row[w]);
-          }
-          for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULL, d, o);
-          if (lane == 0) atomicAdd(&s_bound, d);
-        }
-        __syncthreads();
-        bits3 = pl_bits(min((unsigned long long)n, s_bound), S.tab_bits);
         // level 3: pairs (w, x), w a level-2 vertex, x in N(w) below u; pass 0
         // claims x, pass 1 adds w's row into x's pair row
         for (int pass = 0; pass < 2; pass++) {
           for (int i = wib; i < n2; i += NW) {
-            const int32_t w = (int32_t)(T2[L2[i]].x - 1u);
+            const int32_t w = L2[i];
             const int cw = colors[w];
             const uint4 r0 = *(const uint4 *)(W2 + (int64_t)i * 8);
             const uint4 r1 = *(const uint4 *)(W2 + (int64_t)i * 8 + 4);
@@ -754,20 +685,17 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
               if (x < u) {
                 const int cx = colors[x];
                 if (cx != cu && cx != cw) {
-                  bool any = false;
+                  if (pass == 0) {
+                    bool any = false;
 #pragma unroll
-                  for (int c = 0; c < 8; c++) any = any || (row[c] != 0u && c != cx);
-                  if (any) {
-                    if (pass == 0) {
-                      const int sl = pl_claim(T3, bits3, x);
-                      if (sl >= 0) L3[atomicAdd(&s_n3, 1)] = sl;
-                    } else {
-                      const int64_t ix = pl_find(T3, bits3, x) - 1;
+                    for (int c = 0; c < 8; c++) any = any || (row[c] != 0u && c != cx);
+                    if (any && atomicCAS(id3 + x, 0, -1) == 0) L3[atomicAdd(&s_n3, 1)] = x;
+                  } else {
+                    const int ix = id3[x];  // numbered in pass 0 whenever a row entry below applies
 #pragma unroll
-                      for (int c = 0; c < 8; c++) {
-                        const uint32_t t = row[c];
-                        if (t && c != cx) atomicAdd(W3 + ix * 16 + pair_idx(cw, c), t);
-                      }
+                    for (int c = 0; c < 8; c++) {
+                      const uint32_t t = row[c];
+                      if (t && c != cx) atomicAdd(W3 + (int64_t)(ix - 1) * 16 + pair_idx(cw, c), t);
                     }
                   }
                 }
@@ -777,7 +705,7 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
           }
           __syncthreads();
           if (pass == 0) {
-            for (int i = tid; i < s_n3; i += kPlThreads) T3[L3[i]].y = (uint32_t)(i + 1);
+            for (int i = tid; i < s_n3; i += kPlThreads) id3[L3[i]] = i + 1;
             __syncthreads();
           }
         }
@@ -786,7 +714,7 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
       const int nx = L >= 5 ? s_n3 : n2;
       u64 mine = 0;
       for (int i = tid; i < nx; i += kPlThreads) {
-        const int32_t x = (int32_t)((L >= 5 ? T3[L3[i]].x : T2[L2[i]].x) - 1u);
+        const int32_t x = L >= 5 ? L3[i] : L2[i];
         const int cx = colors[x];
         const uint32_t fm = ((1u << k) - 1u) & ~((1u << cu) | (1u << cx));
         int f[4];
@@ -802,7 +730,7 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
           mine = add_ck(mine, mul_ck(2ull, mul_ck(a0, a1, ovf), ovf), ovf);
         } else if (L == 5) {
           const uint32_t *w3 = W3 + (int64_t)i * 16;
-          const int ix = pl_find(T2, bits2, x);  // x's level-2 row (paths u-v-x), if x was reached at level 2
+          const int ix = id2[x];  // x's level-2 row (paths u-v-x), if x was reached at level 2
           if (ix > 0) {
             const uint32_t *w2 = W2 + (int64_t)(ix - 1) * 8;
             u64 t = mul_ck((u64)w2[f[0]], (u64)w3[pair_idx(f[1], f[2])], ovf);
@@ -824,22 +752,21 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
         if (old + mine < old) ovf = 1;
       }
       __syncthreads();
-      // everything back to zero: rows by local index, table entries through the lists
+      // everything back to zero: rows by local index, ids through the lists
       if (L >= 5) {
         for (int i = tid; i < s_n3; i += kPlThreads) {
-          T3[L3[i]] = make_uint2(0u, 0u);
+          id3[L3[i]] = 0;
           L3[i] = 0;
           uint4 *z = (uint4 *)(W3 + (int64_t)i * 16);
           z[0] = z[1] = z[2] = z[3] = make_uint4(0, 0, 0, 0);
         }
       }
       for (int i = tid; i < n2; i += kPlThreads) {
-        T2[L2[i]] = make_uint2(0u, 0u);
+        id2[L2[i]] = 0;
         L2[i] = 0;
         uint4 *z = (uint4 *)(W2 + (int64_t)i * 8);
         z[0] = z[1] = make_uint4(0, 0, 0, 0);
       }
-      (void)bits3;
     }
     if (ovf) atomicOr(&s_ovf, 1u);
     __syncthreads();
@@ -852,26 +779,6 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
     }
     __syncthreads();
   }
-}
-
-size_t pl_layout(PlScratch &S, int64_t n, int L) {
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    size_t o = off;
-    off += (bytes + 255) & ~(size_t)255;
-    return o;
-  };
-  int bits = 6;
-  while ((int64_t)1 << bits < 2 * n) bits++;
-  S.tab_bits = bits;
-  S.o_rows2 = take((size_t)n * 32);
-  S.o_rows3 = L >= 5 ? take((size_t)n * 64) : 0;
-  S.o_tab2 = take((size_t)8 << bits);
-  S.o_tab3 = L >= 5 ? take((size_t)8 << bits) : 0;
-  S.o_list2 = take((size_t)n * 4);
-  S.o_list3 = L >= 5 ? take((size_t)n * 4) : 0;
-  S.slot_bytes = off;
-  return off;
 }
 
 // Launch the per-CTA push kernel on caller-provided scratch (no allocation
@@ -894,7 +801,19 @@ int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank) {
   if (end_rank <= 0) return CC_OK;
   const int64_t n = a.g.n;
   PlScratch S;
-  pl_layout(S, n, a.L);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  S.o_w2 = take((size_t)n * 32);
+  S.o_w3 = a.L >= 5 ? take((size_t)n * 64) : 0;
+  S.o_mark = take((size_t)n * 4);
+  S.o_id3 = a.L >= 5 ? take((size_t)n * 4) : 0;
+  S.o_l2 = take((size_t)n * 4);
+  S.o_l3 = a.L >= 5 ? take((size_t)n * 4) : 0;
+  S.slot_bytes = off;
   // one slot per resident CTA (up to four per SM); without a budget, slots
   // take at most a quarter of the free device memory and 64 GiB.  A scratch
   // already large enough for more slots is used whole, and under stream

@@ -76,8 +76,20 @@ extern "C" int cc_count_cycle_noalloc(int device, void *cuda_stream, int L, int6
   // counts, then as many per-CTA slots as fit (at least one)
   const size_t head = 256;
   const size_t lo_bytes = ((size_t)n * 4 + 255) & ~(size_t)255;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
   PlScratch S;
-  pl_layout(S, n, L);
+  S.o_w2 = take((size_t)n * 32);
+  S.o_w3 = L >= 5 ? take((size_t)n * 64) : 0;
+  S.o_mark = take((size_t)n * 4);
+  S.o_id3 = L >= 5 ? take((size_t)n * 4) : 0;
+  S.o_l2 = take((size_t)n * 4);
+  S.o_l3 = L >= 5 ? take((size_t)n * 4) : 0;
+  S.slot_bytes = off;
   if (head + lo_bytes + S.slot_bytes > kNoAllocScratchBytes) return CC_ERR_INVALID_ARG;  // graph too large
   const int slots = (int)std::min<size_t>(64, (kNoAllocScratchBytes - head - lo_bytes) / S.slot_bytes);
   int prev = 0;

@@ -60,7 +60,7 @@ def test_noalloc_matches_allocating_path(env, gname, graph, L):
 
 def test_noalloc_rejects_too_large_graphs(env):
     torch, P, _ = env
-    n = 700_000  # one scratch slot for this n is beyond the 64 MiB working array
+    n = 700_000  # n * 112 bytes is beyond the 64 MiB working array
     g = gg.erdos_renyi(n, n, 3)
     rp, col, c = _device_inputs(torch, g, np.zeros(n, dtype=np.uint8))
     with pytest.raises(P.CCError) as ei:
