@@ -40,6 +40,9 @@ WORKLOAD = {"graph": "chung_lu", "n": 1_000_000, "mean_deg": 16, "gamma": 2.1, "
             "queries": ["C6", "glasses"], "form": "plain", "colourings_per_query_per_step": 1}
 COLOR_SEED = 1
 BATCH_QUERIES = ["C5", "chord_pendant", "glasses"]
+# DRAM bytes (read + written) of all C6 closure launches of one colouring of
+# the workload at heavy threshold 256, from one ncu capture of the current kernels
+CLOSURE_TRAFFIC_BYTES = 218.6e9
 FLUSH_BYTES = 256 << 20
 
 
@@ -436,7 +439,10 @@ def main():
     achieved = 8.0 * units["C6"] / (per_colouring_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": "C6 root-cycle closure (" + " + ".join(sorted(closure)) + ")",
                 "achieved": achieved, "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "avg_launch_ms": per_colouring_ms,
+                "frac": achieved / peak, "traffic": CLOSURE_TRAFFIC_BYTES,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over every closure launch of one "
+                                  "colouring (profiles/dram_traffic_chunglu1e6_C6_colouring.md)",
+                "avg_launch_ms": per_colouring_ms,
                 "launches_per_colouring": sum(kern[k][1] for k in closure) / args.steps,
                 "share_of_step": clo_ms / ms}
 
