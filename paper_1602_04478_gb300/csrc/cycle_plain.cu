@@ -1,4 +1,6 @@
-// K5 for unannotated root cycles C_L, L = 4, 5, 6 (k = L), heavy sources.
+// K5 for unannotated root cycles C_L, L = 4, 5, 6 (k = L): heavy sources in
+// groups (level build, pull, closure), the other sources one CTA each (the
+// per-CTA push at the end of this file).
 //
 // The same DB closure as cycle.cu / cycle_heavy.cu, with the table layout
 // fixed by the cycle's shape.  For a source u (highest cycle vertex) and a
@@ -22,9 +24,11 @@
 // Only one highest node is computed (h = 0) and the total is multiplied by L.
 //
 // Heavy sources run in groups of 32 (lane b of a warp = source b); A and P
-// live in registers.  P entries are exact in 32 bits: a level-2 row entry is
-// below 2^16 and x has fewer than 2^16 neighbours (the host checks the
-// maximum degree).
+// live in registers.  Two groups are in flight at a time (two scratch
+// banks): their level builds run back to back and, for the push-form groups,
+// one pull pass serves both.  P entries are exact in 32 bits: a level-2 row
+// entry is below 2^16 and x has fewer than 2^16 neighbours (the host checks
+// the maximum degree).
 #include <algorithm>
 
 #include "cc_kernels.h"
