@@ -58,15 +58,19 @@ struct PcGroup {
 };
 
 // ------------------------------ level build ------------------------------
-// grid.y = source b; warps walk the lower neighbours v of u_b and their
+// grid.y = source b (of one or two groups); warps walk the lower neighbours v of u_b and their
 // neighbours w below u_b, 32 at a time (v's row is rank ordered, so the walk
 // stops at the first chunk that reaches u_b).  A level-2 vertex is listed
 // once per source, the warp taking its list slots with one atomic.
 template <int L>
-__global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uint8_t *colors, PcScratch S,
-                                                          PcGroup G) {
+__global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uint8_t *colors, PcScratch SA,
+                                                          PcGroup GA, PcScratch SB, PcGroup GB) {
   constexpr unsigned FULL = 0xffffffffu;
-  const int b = blockIdx.y;
+  // rows 0 .. GA.B-1 of the grid serve group A (bank A), the rest group B
+  const bool second = (int)blockIdx.y >= GA.B;
+  const PcScratch S = second ? SB : SA;
+  const PcGroup &G = second ? GB : GA;
+  const int b = second ? (int)blockIdx.y - GA.B : (int)blockIdx.y;
   const int32_t u = G.u[b];
   const int cu = colors[u];
   const int64_t n = g.n;
@@ -547,8 +551,12 @@ __global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull2(GraphView g, const u
 // grid.y = source b: zero its level-1 membership words and, for its listed
 // level-2 vertices, the membership word, the row and the list entry.
 template <int L>
-__global__ void k_pc_clear(GraphView g, PcScratch S, PcGroup G) {
-  const int b = blockIdx.y;
+__global__ void k_pc_clear(GraphView g, PcScratch SA, PcGroup GA, PcScratch SB, PcGroup GB) {
+  // rows 0 .. GA.B-1 of the grid serve group A (bank A), the rest group B
+  const bool second = (int)blockIdx.y >= GA.B;
+  const PcScratch S = second ? SB : SA;
+  const PcGroup &G = second ? GB : GA;
+  const int b = second ? (int)blockIdx.y - GA.B : (int)blockIdx.y;
   const int64_t n = g.n;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nt = (int64_t)gridDim.x * blockDim.x;
@@ -567,10 +575,15 @@ __global__ void k_pc_clear(GraphView g, PcScratch S, PcGroup G) {
   }
 }
 
-// One lane per source: the group's totals (times the rotation multiplier)
+// One lane per source (one warp per group): the totals (times the rotation multiplier)
 // into the per-vertex split and the count; totals and list counts back to 0.
-__global__ void k_pc_finish(PcScratch S, PcGroup G, int multiplier, u64 *per_vertex, u64 *status) {
-  const int b = threadIdx.x;
+__global__ void k_pc_finish(PcScratch SA, PcGroup GA, PcScratch SB, PcGroup GB, int multiplier, u64 *per_vertex,
+                            u64 *status) {
+  // warp 0: group A, warp 1 (when launched): group B
+  const bool second = threadIdx.x >= 32;
+  const PcScratch S = second ? SB : SA;
+  const PcGroup &G = second ? GB : GA;
+  const int b = threadIdx.x & 31;
   unsigned ovf = 0;
   u64 t = 0;
   if (b < G.B) {
@@ -927,17 +940,23 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
     for (int b = 0; b < G.B; b++) G.u[b] = (int32_t)(top - b);
     return G;
   };
-  auto push_levels = [&](const PcScratch &S, const PcGroup &G) {
+  PcGroup none;
+  none.B = 0;
+  none.umax = 0;
+  // push-form level build of one group (G2.B = 0) or two (banks 0 and 1);
+  // grid rows are sources, the highest source's degree sizes the grid
+  auto push_levels = [&](const PcGroup &G, const PcGroup &G2) {
     const int64_t du = c.cur_graph_row[G.umax + 1] - c.cur_graph_row[G.umax];
     dim3 gl((unsigned)std::max<int64_t>(1, std::min<int64_t>(sms * 2, (du * 32 + kPcThreads - 1) / kPcThreads)),
-            G.B);
-    k_pc_levels<L><<<gl, kPcThreads, 0, c.stream>>>(a.g, a.colors, S, G);
+            G.B + G2.B);
+    k_pc_levels<L><<<gl, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G, S1, G2);
     c.kernels++;
   };
-  auto close_group = [&](const PcScratch &S, const PcGroup &G) {
-    k_pc_clear<L><<<dim3(std::max(1, sms / 8), G.B), 256, 0, c.stream>>>(a.g, S, G);
+  // scratch of one group (bank 0) or two back to zero; totals into the count
+  auto close_groups = [&](const PcGroup &G, const PcGroup &G2) {
+    k_pc_clear<L><<<dim3(std::max(1, sms / 8), G.B + G2.B), 256, 0, c.stream>>>(a.g, S0, G, S1, G2);
     c.kernels++;
-    k_pc_finish<<<1, 32, 0, c.stream>>>(S, G, a.multiplier, a.per_vertex, a.status);
+    k_pc_finish<<<1, G2.B ? 64 : 32, 0, c.stream>>>(S0, G, S1, G2, a.multiplier, a.per_vertex, a.status);
     c.kernels++;
   };
   const size_t anym_bytes = (size_t)((n + 31) / 32) * 4;
@@ -990,8 +1009,7 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
         c.kernels++;
       }
       timing_end(c);
-      close_group(S0, G);
-      if (two) close_group(S1, G2);
+      close_groups(G, two ? G2 : none);
       pulled = true;
       pulled_b1 = pulled_b1 || two;
       top -= two ? 2 * kPcMaxB : kPcMaxB;
@@ -1002,8 +1020,7 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
     const bool two = top - kPcMaxB >= first_rank;
     const PcGroup G2 = two ? group_at(top - kPcMaxB) : G;
     timing_begin(c, "cycle_plain_levels");
-    push_levels(S0, G);
-    if (two) push_levels(S1, G2);
+    push_levels(G, two ? G2 : none);
     timing_end(c);
     timing_begin(c, "cycle_plain_pull");
     if (two)
@@ -1012,8 +1029,7 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
       k_pc_pull<L><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, tag, S0, G, a.colors, a.status);
     c.kernels++;
     timing_end(c);
-    close_group(S0, G);
-    if (two) close_group(S1, G2);
+    close_groups(G, two ? G2 : none);
     top -= two ? 2 * kPcMaxB : kPcMaxB;
   }
   // the scratch is all zero between launches
