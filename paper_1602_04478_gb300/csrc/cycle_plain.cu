@@ -607,15 +607,39 @@ __global__ void k_pc_finish(PcScratch SA, PcGroup GA, PcScratch SB, PcGroup GB, 
 //
 // The rows of one source are compact: a vertex reached at level 2 (3) gets
 // the next local index, and its row lives at that index, so the rows a source
-// touches are contiguous and stay in cache.  Each level is walked twice: the
-// first walk claims the vertices (id[v] = -1 marks a claim, the claimant
-// lists it), the CTA then numbers the list (id[v] = index + 1), and the second
-// walk adds into the numbered rows.
+// touches are contiguous and stay in cache.  Each level is walked once: a
+// thread reaching v swaps id[v] from 0 to -1; the winner takes the next index,
+// lists v and publishes id[v] = index + 1, every other thread reads the index
+// from the swap's old value (or, in the short window before the winner
+// publishes, waits for it, with an iteration limit that reports
+// CC_ERR_TIMEOUT), and then adds into v's row.
 constexpr int kPlThreads = 256;
 
 __device__ __forceinline__ int pair_idx(int a, int b) {
   int hi = a > b ? a : b, lo = a > b ? b : a;
   return hi * (hi - 1) / 2 + lo;
+}
+
+constexpr int kPlSpinLimit = 1 << 22;
+
+// Local index of v at one level: claimed (and listed) by the first thread to
+// reach it, read by the others; -1 when the wait for the claimant gave up.
+__device__ __forceinline__ int pl_index(int32_t *id, int32_t v, int32_t *list, int *s_n, unsigned &tmo) {
+  int old = atomicCAS(id + v, 0, -1);
+  if (old == 0) {
+    const int i = atomicAdd(s_n, 1);
+    list[i] = v;
+    atomicExch(id + v, i + 1);
+    return i;
+  }
+  for (int spins = 0; old < 0; spins++) {
+    if (spins == kPlSpinLimit) {
+      tmo = 1u;
+      return -1;
+    }
+    old = *(volatile int32_t *)(id + v);
+  }
+  return old - 1;
 }
 
 template <int L>
@@ -649,28 +673,61 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
     const int cu = colors[u];
     const int64_t ub = g.row[u];
     const int du = g.lo_cnt[u];
-    unsigned ovf = 0;
+    unsigned ovf = 0, tmo = 0;
     if (du >= 2) {
-      // level 2: pairs (v, w), v in N<(u), w in N(v) below u; pass 0 claims w,
-      // pass 1 counts chi(v) into w's row.  v's row is rank ordered: it is
-      // walked to the first chunk that reaches u.
-      for (int pass = 0; pass < 2; pass++) {
-        for (int i = wib; i < du; i += NW) {
-          const int32_t v = __ldg(g.col + ub + i);
-          const int cv = colors[v];
-          if (cv == cu) continue;
-          const int64_t vb = g.row[v], vend = g.row[v + 1];
-          for (int64_t e0 = vb; e0 < vend; e0 += 32) {
+      // level 2: pairs (v, w), v in N<(u), w in N(v) below u: chi(v) counted
+      // into w's row.  v's row is rank ordered: it is walked to the first
+      // chunk that reaches u.
+      for (int i = wib; i < du; i += NW) {
+        const int32_t v = __ldg(g.col + ub + i);
+        const int cv = colors[v];
+        if (cv == cu) continue;
+        const int64_t vb = g.row[v], vend = g.row[v + 1];
+        for (int64_t e0 = vb; e0 < vend; e0 += 32) {
+          const int64_t e = e0 + lane;
+          const int32_t w = e < vend ? __ldg(g.col + e) : INT32_MAX;
+          const bool done = __any_sync(FULL, w >= u);
+          if (w < u) {
+            const int cw = colors[w];
+            if (cw != cu && cw != cv) {
+              const int iw = pl_index(id2, w, L2, &s_n2, tmo);
+              if (iw >= 0) atomicAdd(W2 + (int64_t)iw * 8 + cv, 1u);
+            }
+          }
+          if (done) break;
+        }
+      }
+      __syncthreads();
+      const int n2 = s_n2;
+      if (L >= 5) {
+        // level 3: pairs (w, x), w a level-2 vertex, x in N(w) below u: w's
+        // row added into x's pair row
+        for (int i = wib; i < n2; i += NW) {
+          const int32_t w = L2[i];
+          const int cw = colors[w];
+          const uint4 r0 = *(const uint4 *)(W2 + (int64_t)i * 8);
+          const uint4 r1 = *(const uint4 *)(W2 + (int64_t)i * 8 + 4);
+          const uint32_t row[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+          const int64_t wb = g.row[w], wend = g.row[w + 1];
+          for (int64_t e0 = wb; e0 < wend; e0 += 32) {
             const int64_t e = e0 + lane;
-            const int32_t w = e < vend ? __ldg(g.col + e) : INT32_MAX;
-            const bool done = __any_sync(FULL, w >= u);
-            if (w < u) {
-              const int cw = colors[w];
-              if (cw != cu && cw != cv) {
-                if (pass == 0) {
-                  if (atomicCAS(id2 + w, 0, -1) == 0) L2[atomicAdd(&s_n2, 1)] = w;
-                } else {
-                  atomicAdd(W2 + (int64_t)(id2[w] - 1) * 8 + cv, 1u);
+            const int32_t x = e < wend ? __ldg(g.col + e) : INT32_MAX;
+            const bool done = __any_sync(FULL, x >= u);
+            if (x < u) {
+              const int cx = colors[x];
+              if (cx != cu && cx != cw) {
+                bool any = false;
+#pragma unroll
+                for (int c = 0; c < 8; c++) any = any || (row[c] != 0u && c != cx);
+                if (any) {
+                  const int ix = pl_index(id3, x, L3, &s_n3, tmo);
+                  if (ix >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 8; c++) {
+                      const uint32_t t = row[c];
+                      if (t && c != cx) atomicAdd(W3 + (int64_t)ix * 16 + pair_idx(cw, c), t);
+                    }
+                  }
                 }
               }
             }
@@ -678,54 +735,6 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
           }
         }
         __syncthreads();
-        if (pass == 0) {
-          for (int i = tid; i < s_n2; i += kPlThreads) id2[L2[i]] = i + 1;
-          __syncthreads();
-        }
-      }
-      const int n2 = s_n2;
-      if (L >= 5) {
-        // level 3: pairs (w, x), w a level-2 vertex, x in N(w) below u; pass 0
-        // claims x, pass 1 adds w's row into x's pair row
-        for (int pass = 0; pass < 2; pass++) {
-          for (int i = wib; i < n2; i += NW) {
-            const int32_t w = L2[i];
-            const int cw = colors[w];
-            const uint4 r0 = *(const uint4 *)(W2 + (int64_t)i * 8);
-            const uint4 r1 = *(const uint4 *)(W2 + (int64_t)i * 8 + 4);
-            const uint32_t row[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-            const int64_t wb = g.row[w], wend = g.row[w + 1];
-            for (int64_t e0 = wb; e0 < wend; e0 += 32) {
-              const int64_t e = e0 + lane;
-              const int32_t x = e < wend ? __ldg(g.col + e) : INT32_MAX;
-              const bool done = __any_sync(FULL, x >= u);
-              if (x < u) {
-                const int cx = colors[x];
-                if (cx != cu && cx != cw) {
-                  if (pass == 0) {
-                    bool any = false;
-#pragma unroll
-                    for (int c = 0; c < 8; c++) any = any || (row[c] != 0u && c != cx);
-                    if (any && atomicCAS(id3 + x, 0, -1) == 0) L3[atomicAdd(&s_n3, 1)] = x;
-                  } else {
-                    const int ix = id3[x];  // numbered in pass 0 whenever a row entry below applies
-#pragma unroll
-                    for (int c = 0; c < 8; c++) {
-                      const uint32_t t = row[c];
-                      if (t && c != cx) atomicAdd(W3 + (int64_t)(ix - 1) * 16 + pair_idx(cw, c), t);
-                    }
-                  }
-                }
-              }
-              if (done) break;
-            }
-          }
-          __syncthreads();
-          if (pass == 0) {
-            for (int i = tid; i < s_n3; i += kPlThreads) id3[L3[i]] = i + 1;
-            __syncthreads();
-          }
-        }
       }
       // closure at the meeting vertices (level 3 for L >= 5, level 2 for L = 4)
       const int nx = L >= 5 ? s_n3 : n2;
@@ -786,6 +795,7 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
       }
     }
     if (ovf) atomicOr(&s_ovf, 1u);
+    if (tmo) atomicOr(status + ST_TIMEOUT, 1ull);
     __syncthreads();
     if (tid == 0) {
       unsigned o = s_ovf;
