@@ -41,8 +41,9 @@ WORKLOAD = {"graph": "chung_lu", "n": 1_000_000, "mean_deg": 16, "gamma": 2.1, "
 COLOR_SEED = 1
 BATCH_QUERIES = ["C5", "chord_pendant", "glasses"]
 # DRAM bytes (read + written) of all C6 closure launches of one colouring of
-# the workload at heavy threshold 256, from one ncu capture of the current kernels
-CLOSURE_TRAFFIC_BYTES = 220.8e9
+# the workload at heavy threshold 384 (the autotuned one), from one ncu
+# capture of the current kernels
+CLOSURE_TRAFFIC_BYTES = 248.2e9
 FLUSH_BYTES = 256 << 20
 
 
