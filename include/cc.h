@@ -244,7 +244,7 @@ int cc_kernel_launches(cc_ctx *ctx, uint64_t *launches);
  * receives the count, equal to cc_count's for the same graph, colours and
  * query.  Working memory is one static device array of 64 MiB inside the
  * library, held by every GPU that loads it until the process exits; the
- * graph must fit in it: n * 112 bytes (L = 5, 6) or n * 44 bytes (L = 4)
+ * graph must fit in it: n * 112 bytes (L = 5, 6) or n * 40 bytes (L = 4)
  * plus n * 4 bytes and 256 bytes at most 64 MiB, else CC_ERR_INVALID_ARG.
  * Maximum degree must stay below 65536 (CC_ERR_INVALID_ARG otherwise);
  * unsorted rows, out-of-range ids, self-loops or colours >= L give
