@@ -920,7 +920,7 @@ static int push_work(Ctx &c, const GraphView &g, const int64_t **out) {
 // A group takes the pull-form level build while its push work exceeds this
 // many times the edges of the rows below its highest source (the pull form
 // scans those rows once, without atomics).
-constexpr double kPullLevelsRatio = 0.7;
+constexpr double kPullLevelsRatio = 0.5;
 
 template <int L>
 static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcScratch *SB, const uint32_t *tag) {
