@@ -125,8 +125,25 @@ def from_edges(n: int, edges) -> Graph:
 
 
 def complete_graph(n: int) -> Graph:
-    e = [(a, b) for a in range(n) for b in range(a + 1, n)]
-    return from_edges(n, e)
+    """K_n, built directly as a CSR (row v holds every other vertex)."""
+    if n <= 1:
+        return Graph(n=max(n, 0), row_ptr=np.zeros(max(n, 0) + 1, dtype=np.int64),
+                     col=np.zeros(0, dtype=np.int32), name=f"complete_n{n}")
+    ids = np.arange(n, dtype=np.int32)
+    col = np.broadcast_to(ids, (n, n))[~np.eye(n, dtype=bool)].astype(np.int32)
+    row_ptr = np.arange(n + 1, dtype=np.int64) * (n - 1)
+    return Graph(n=n, row_ptr=row_ptr, col=np.ascontiguousarray(col), name=f"complete_n{n}")
+
+
+def wheel_with_chords(n_ring: int = 9000, chords: int = 30000, seed: int = 11) -> Graph:
+    """A hub adjacent to all ring vertices 1..n_ring, the ring itself and
+    `chords` random chords between ring vertices: one vertex of very high
+    degree and many of moderate degree."""
+    rng = np.random.default_rng(seed)
+    n = n_ring + 1
+    e = [(0, i) for i in range(1, n)] + [(i, i % n_ring + 1) for i in range(1, n)]
+    e += [tuple(x) for x in rng.integers(1, n, size=(chords, 2)) if x[0] != x[1]]
+    return from_edges(n, np.array(e))
 
 
 def relabel(g: Graph, perm: np.ndarray) -> Graph:
@@ -155,6 +172,13 @@ QUERIES = {
     "glasses": (7, [(0, 1), (1, 2), (2, 0), (4, 5), (5, 6), (6, 4), (2, 3), (3, 4)]),
     # 6-cycle 0..5 with pendants 6-0 and 7-3 (opposite cycle vertices)
     "C6_2pendants": (8, [(i, (i + 1) % 6) for i in range(6)] + [(0, 6), (3, 7)]),
+    # the same with the pendants on adjacent cycle vertices, or both on one
+    "C6_2pendants_adj": (8, [(i, (i + 1) % 6) for i in range(6)] + [(0, 6), (1, 7)]),
+    "C6_2pendants_same": (8, [(i, (i + 1) % 6) for i in range(6)] + [(0, 6), (0, 7)]),
+    # 5-cycle with a path of two edges hanging from one node
+    "C5_pendant_path": (7, [(i, (i + 1) % 5) for i in range(5)] + [(0, 5), (5, 6)]),
+    "C7": cycle(7),
+    "C8": cycle(8),
 }
 
 

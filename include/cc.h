@@ -81,6 +81,21 @@ int cc_set_memory_budget(cc_ctx *ctx, size_t bytes);
  * changes only the speed, never the counts. */
 int cc_set_heavy_degree(cc_ctx *ctx, int degree);
 
+/* Procedure for root cycle blocks of length >= 4 (Section 5).
+ * CC_PROC_DB (default): the degree-based procedure -- matches split by the
+ * cycle node holding the highest vertex in the degree order (Eq. 1), paths
+ * extended only through lower vertices (Procedures 1-2, general-cycle
+ * figure).  CC_PROC_PS: the path-splitting procedure without vertex order
+ * -- one split of the cycle at a_0 and its opposite node, paths extended
+ * through any vertex (Procedures 1-2 of the PS algorithm figure).  Both give
+ * the same counts; PS does far more work on skewed graphs and runs on the
+ * library's general per-source kernel only.  cc_count_per_vertex splits a
+ * PS count by the image of a_0.  Triangle and leaf blocks are the same under
+ * both. */
+#define CC_PROC_DB 0
+#define CC_PROC_PS 1
+int cc_set_procedure(cc_ctx *ctx, int procedure);
+
 /* Copy a data graph to the device.  row_ptr[n+1] (int64) and col[nnz]
  * (int32, caller's vertex ids) describe a symmetric simple graph: each
  * undirected edge appears in both rows, no self-loops, no duplicates.
@@ -126,6 +141,18 @@ int cc_set_decomposition(cc_ctx *ctx, int32_t query_id, const int32_t *block_seq
 int cc_plan_inspect(int k, int n_edges, const int32_t *edges, const int32_t *block_seq, int seq_len,
                     int32_t *out, int cap, int64_t *aut);
 
+/* Host-only: every decomposition tree of a query (Section 5.3), one record
+ * per distinct tree -- sequence length m, supported (1 when the library has
+ * kernels for every block), the paper's ranking factors (longest cycle
+ * block, number of boundary nodes, number of annotations, each summed over
+ * the blocks), 1 when it is the tree cc_set_query picks, then the m-word
+ * contraction sequence in cc_set_decomposition's block_seq format -- into
+ * out[cap].  *n_plans (nullable) receives the number of trees.  Returns the
+ * number of int32 words (more than cap means truncated) or a CC_ERR_ code.
+ * cc_set_query picks, among the supported trees, the least by the paper's
+ * factors in order (Section 5.3's heuristic). */
+int cc_plan_enumerate(int k, int n_edges, const int32_t *edges, int32_t *out, int cap, int *n_plans);
+
 /* Query facts: k, aut(Q), number of blocks, longest cycle block. */
 int cc_query_info(cc_ctx *ctx, int32_t query_id, int *k, int64_t *aut, int *n_blocks,
                   int *longest_cycle);
@@ -143,7 +170,10 @@ int cc_clear_colors(cc_ctx *ctx, int32_t graph_id);
  * colorful[T]: colourful match counts (uint64).  estimate[T] (nullable):
  * colorful * k^k / k! / aut(Q), the subgraph-count estimate of that trial.
  * aut (nullable): aut(Q).  On CC_ERR_OVERFLOW the overflowing trials'
- * colorful entries are UINT64_MAX and the other trials are still filled. */
+ * colorful entries are UINT64_MAX and the other trials are still filled.
+ * A trial's uint64 result is fixed once its count passes 2^64-1, so the
+ * general root-cycle path (annotated cycles, cycles longer than 6) stops
+ * its work there. */
 int cc_count(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int first_trial, int T,
              uint64_t *colorful, double *estimate, double *aut);
 
@@ -210,15 +240,34 @@ int cc_server_stats(cc_server *s, int64_t *waiting, int64_t *running, size_t *by
 /* One trial, and the count split by vertex: for a root cycle block the
  * colourful matches whose highest root-cycle vertex (degree order) is v;
  * for a root that is a single node, the matches mapping that node to v.
- * per_vertex[n] is indexed by the caller's vertex ids and sums to *total. */
+ * per_vertex[n] is indexed by the caller's vertex ids and sums to *total.
+ * On CC_ERR_OVERFLOW *total is UINT64_MAX and the split is not defined (the
+ * general root-cycle path stops once the count has passed 2^64-1). */
 int cc_count_per_vertex(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int trial,
                         uint64_t *per_vertex, uint64_t *total);
 
 /* Structural work of one colouring of query_id on graph_id in edge-subset
- * updates (independent of the colouring; see the design notes): the sum,
- * over every table-building step, of the data edges it scans times the
- * signature slots of the rows it extends. */
+ * updates (independent of the colouring): the sum, over every
+ * table-building step, of the data edges it scans times the signature slots
+ * of the rows it extends.  For a root cycle of length L these are, for every
+ * source u (highest cycle vertex) with at least two lower neighbours and
+ * both halves (floor(L/2) and ceil(L/2) hops), the edges from each level-j
+ * vertex to vertices below u, times C(k-2, j-1) slots (one slot at j = 0). */
 int cc_work_units(cc_ctx *ctx, int32_t graph_id, int32_t query_id, double *units);
+
+/* The same structural work split by the plan's stages (contraction order,
+ * kinds as in cc_plan_inspect: 0 leaf, 1 triangle, 2 root cycle, 3 root
+ * node).  For stage i < cap: kind[i], units[i] (edge-subset updates),
+ * alg_bytes[i] (the stage's algorithmic bytes: for a leaf join 8 per update
+ * that gathers a table entry, 4 per directed edge for the neighbour id and
+ * 8 per table entry read from the annotating node block or written; for a
+ * triangle block 4 per wedge scanned and 8 per output entry; for a root
+ * cycle 4 per data edge scanned; for a root node 8 per vertex) and
+ * scans[8 i + j] (root cycle: data edges scanned out of level j, both halves
+ * summed; 0 for other stages).  Any output may be NULL.  Returns the number
+ * of stages or a CC_ERR_ code. */
+int cc_work_detail(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int cap, int32_t *kind, double *units,
+                   double *alg_bytes, double *scans);
 
 /* Kernel timing: when enabled, the library brackets each kernel launch with
  * CUDA events on its stream and accumulates the time per kernel name.
@@ -248,8 +297,11 @@ int cc_kernel_launches(cc_ctx *ctx, uint64_t *launches);
  * plus n * 4 bytes and 256 bytes at most 64 MiB, else CC_ERR_INVALID_ARG.
  * Maximum degree must stay below 65536 (CC_ERR_INVALID_ARG otherwise);
  * unsorted rows, out-of-range ids, self-loops or colours >= L give
- * CC_ERR_BAD_GRAPH.  Work is issued on cuda_stream (a cudaStream_t, NULL for
- * the legacy stream) and the call returns when the count is on the host.
+ * CC_ERR_BAD_GRAPH; CC_ERR_TIMEOUT when the kernel's bounded wait gave up
+ * (a contribution was skipped, so no count is returned); CC_ERR_OVERFLOW
+ * with *count = UINT64_MAX when the count exceeds 2^64-1.  Work is issued on
+ * cuda_stream (a cudaStream_t, NULL for the legacy stream); the call
+ * synchronises that stream twice and returns when the count is on the host.
  * The first call on a device looks up the array's device address with
  * cudaGetSymbolAddress; make that first call before any stream capture on
  * that device.  All calls share the one array (each call clears what it

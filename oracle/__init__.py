@@ -71,7 +71,7 @@ def _load():
                                     ctypes.c_int, I64P, I32P, ctypes.c_int, U8P, U64P, U64P,
                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         lib.or_cycle_units.argtypes = [ctypes.c_int64, I64P, I32P, ctypes.c_int, ctypes.c_int, U8P,
-                                       ctypes.POINTER(ctypes.c_double)]
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         lib.or_cycle_units.restype = ctypes.c_double
         lib.or_decompose.argtypes = [ctypes.c_int, ctypes.c_int, I32P, I32P, ctypes.c_int, I32P,
                                      ctypes.c_int, I32P, ctypes.c_int, I32P]
@@ -243,11 +243,20 @@ def all_plans(k, edges, limit=10000):
     return plans
 
 
-def cycle_units(g, L, k, source_filter=None, per_source=False):
-    """Structural DB work (edge-subset updates) of a plain root L-cycle."""
+def cycle_units(g, L, k, source_filter=None, per_source=False, scans=False):
+    """Structural DB work (edge-subset updates) of a plain root L-cycle.
+
+    per_source: also the units by source; scans: also the data edges scanned
+    out of each level (list of 8, both halves summed)."""
     rp, cl = _graph_arrays(g)
     filt = np.ascontiguousarray(source_filter, dtype=np.uint8) if source_filter is not None else None
     ps = np.zeros(max(g.n, 1), dtype=np.float64) if per_source else None
+    sc = np.zeros(8, dtype=np.float64) if scans else None
     tot = _load().or_cycle_units(g.n, _p(rp, ctypes.c_int64), _p(cl, ctypes.c_int32), L, k,
-                                 _p(filt, ctypes.c_uint8), _p(ps, ctypes.c_double))
-    return (tot, ps[:g.n]) if per_source else tot
+                                 _p(filt, ctypes.c_uint8), _p(ps, ctypes.c_double), _p(sc, ctypes.c_double))
+    out = [tot]
+    if per_source:
+        out.append(ps[:g.n])
+    if scans:
+        out.append([float(x) for x in sc])
+    return tuple(out) if len(out) > 1 else tot

@@ -887,9 +887,11 @@ extern "C" int or_decompose(int k, int ne, const int32_t *qedges, const int32_t 
 // slots (level 0: one slot).  One highest-node choice (rotations of a plain
 // cycle give equal counts).  A source with fewer than two lower neighbours
 // closes no cycle and does no work.  Independent of the colouring.
-// source_filter (nullable): only these sources; per_source (nullable): units by u.
+// source_filter (nullable): only these sources; per_source (nullable): units by u;
+// scans (nullable, 8 entries): edges scanned out of level j, both halves summed
+// (the CSR reads behind the units).
 extern "C" double or_cycle_units(int64_t n, const int64_t *row_ptr, const int32_t *col, int L, int k,
-                                 const uint8_t *source_filter, double *per_source) {
+                                 const uint8_t *source_filter, double *per_source, double *scans) {
   DGraph g;
   load_graph(g, n, row_ptr, col);
   std::vector<int64_t> rank = degree_rank(g);
@@ -918,6 +920,7 @@ extern "C" double or_cycle_units(int64_t n, const int64_t *row_ptr, const int32_
           for (int32_t w : g.adj[v]) {
             if (rank[w] >= rank[u]) continue;
             mine += slots;
+            if (scans && j < 8) scans[j] += 1.0;
             if (mark[w] != tag) { mark[w] = tag; next.push_back(w); }
           }
         level.swap(next);

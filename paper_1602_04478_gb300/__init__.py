@@ -30,9 +30,12 @@ ERRORS = {
 }
 EXPORTED = [
     "cc_create", "cc_destroy", "cc_set_allocator", "cc_set_memory_budget", "cc_set_heavy_degree",
+    "cc_set_procedure",
     "cc_load_csr", "cc_free_graph",
-    "cc_graph_info", "cc_set_query", "cc_set_decomposition", "cc_plan_inspect", "cc_query_info", "cc_set_coloring_seed",
-    "cc_set_colors", "cc_clear_colors", "cc_count", "cc_count_per_vertex", "cc_work_units", "cc_set_timing",
+    "cc_graph_info", "cc_set_query", "cc_set_decomposition", "cc_plan_inspect", "cc_plan_enumerate", "cc_query_info",
+    "cc_set_coloring_seed",
+    "cc_set_colors", "cc_clear_colors", "cc_count", "cc_count_per_vertex", "cc_work_units", "cc_work_detail",
+    "cc_set_timing",
     "cc_get_timing", "cc_reset_timing", "cc_kernel_launches", "cc_count_cycle_noalloc", "cc_count_batch", "cc_set_graph_capture",
     "cc_autotune", "cc_server_create", "cc_server_destroy", "cc_server_load_csr", "cc_server_set_query",
     "cc_server_set_coloring_seed", "cc_server_submit", "cc_server_poll", "cc_server_stats", "cc_strerror",
@@ -65,63 +68,83 @@ def build(force: bool = False) -> str:
     return _build.build(force=force)
 
 
+def load_library(path: str):
+    """A CDLL of `path` with the C-ABI's argument and result types set."""
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I32, I64, U64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    I32P, I64P = ctypes.POINTER(I32), ctypes.POINTER(I64)
+    U64P, U8P, DP = ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "cc_create": ([ctypes.POINTER(P), ctypes.c_int, P], ctypes.c_int),
+        "cc_destroy": ([P], None),
+        "cc_set_allocator": ([P, ALLOC_FN, FREE_FN, P], ctypes.c_int),
+        "cc_set_memory_budget": ([P, ctypes.c_size_t], ctypes.c_int),
+        "cc_set_heavy_degree": ([P, ctypes.c_int], ctypes.c_int),
+        "cc_set_procedure": ([P, ctypes.c_int], ctypes.c_int),
+        "cc_load_csr": ([P, I64, I64P, I32P, I64, I32P], ctypes.c_int),
+        "cc_free_graph": ([P, I32], ctypes.c_int),
+        "cc_graph_info": ([P, I32, I64P, I64P, I64P], ctypes.c_int),
+        "cc_set_query": ([P, ctypes.c_int, ctypes.c_int, I32P, I32P], ctypes.c_int),
+        "cc_set_decomposition": ([P, I32, I32P, ctypes.c_int], ctypes.c_int),
+        "cc_plan_inspect": ([ctypes.c_int, ctypes.c_int, I32P, I32P, ctypes.c_int, I32P, ctypes.c_int, I64P],
+                            ctypes.c_int),
+        "cc_plan_enumerate": ([ctypes.c_int, ctypes.c_int, I32P, I32P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+                              ctypes.c_int),
+        "cc_query_info": ([P, I32, ctypes.POINTER(ctypes.c_int), I64P, ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cc_set_coloring_seed": ([P, U64], ctypes.c_int),
+        "cc_set_colors": ([P, I32, U8P, ctypes.c_int], ctypes.c_int),
+        "cc_clear_colors": ([P, I32], ctypes.c_int),
+        "cc_count": ([P, I32, I32, ctypes.c_int, ctypes.c_int, U64P, DP, DP], ctypes.c_int),
+        "cc_count_per_vertex": ([P, I32, I32, ctypes.c_int, U64P, U64P], ctypes.c_int),
+        "cc_work_units": ([P, I32, I32, DP], ctypes.c_int),
+        "cc_work_detail": ([P, I32, I32, ctypes.c_int, I32P, DP, DP, DP], ctypes.c_int),
+        "cc_set_timing": ([P, ctypes.c_int], ctypes.c_int),
+        "cc_get_timing": ([P, ctypes.c_char_p, DP, I64P, ctypes.c_int], ctypes.c_int),
+        "cc_reset_timing": ([P], ctypes.c_int),
+        "cc_kernel_launches": ([P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "cc_count_cycle_noalloc": ([ctypes.c_int, P, ctypes.c_int, I64, P, P, P, U64P], ctypes.c_int),
+        "cc_count_batch": ([P, ctypes.POINTER(cc_request), ctypes.c_int, U64P, ctypes.POINTER(ctypes.c_int)],
+                           ctypes.c_int),
+        "cc_set_graph_capture": ([P, ctypes.c_int], ctypes.c_int),
+        "cc_autotune": ([P, I32, I32, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cc_server_create": ([ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
+        "cc_server_destroy": ([P], None),
+        "cc_server_load_csr": ([P, I64, I64P, I32P, I64, I32P], ctypes.c_int),
+        "cc_server_set_query": ([P, ctypes.c_int, ctypes.c_int, I32P, I32P], ctypes.c_int),
+        "cc_server_set_coloring_seed": ([P, U64], ctypes.c_int),
+        "cc_server_submit": ([P, I32, I32, ctypes.c_int, ctypes.c_int, U64P, I64P], ctypes.c_int),
+        "cc_server_poll": ([P, ctypes.POINTER(cc_server_result), ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "cc_server_stats": ([P, I64P, I64P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "cc_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
 def lib():
     """The loaded C library (built first if its sources changed)."""
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH) or _build.build() != LIB_PATH:
             raise ImportError("libcc.so is missing; build it with paper_1602_04478_gb300._build.build()")
-        L = ctypes.CDLL(LIB_PATH)
-        P = ctypes.c_void_p
-        I32, I64, U64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
-        I32P, I64P = ctypes.POINTER(I32), ctypes.POINTER(I64)
-        U64P, U8P, DP = ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_double)
-        sig = {
-            "cc_create": ([ctypes.POINTER(P), ctypes.c_int, P], ctypes.c_int),
-            "cc_destroy": ([P], None),
-            "cc_set_allocator": ([P, ALLOC_FN, FREE_FN, P], ctypes.c_int),
-            "cc_set_memory_budget": ([P, ctypes.c_size_t], ctypes.c_int),
-            "cc_set_heavy_degree": ([P, ctypes.c_int], ctypes.c_int),
-            "cc_load_csr": ([P, I64, I64P, I32P, I64, I32P], ctypes.c_int),
-            "cc_free_graph": ([P, I32], ctypes.c_int),
-            "cc_graph_info": ([P, I32, I64P, I64P, I64P], ctypes.c_int),
-            "cc_set_query": ([P, ctypes.c_int, ctypes.c_int, I32P, I32P], ctypes.c_int),
-            "cc_set_decomposition": ([P, I32, I32P, ctypes.c_int], ctypes.c_int),
-            "cc_plan_inspect": ([ctypes.c_int, ctypes.c_int, I32P, I32P, ctypes.c_int, I32P, ctypes.c_int, I64P],
-                                ctypes.c_int),
-            "cc_query_info": ([P, I32, ctypes.POINTER(ctypes.c_int), I64P, ctypes.POINTER(ctypes.c_int),
-                               ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
-            "cc_set_coloring_seed": ([P, U64], ctypes.c_int),
-            "cc_set_colors": ([P, I32, U8P, ctypes.c_int], ctypes.c_int),
-            "cc_clear_colors": ([P, I32], ctypes.c_int),
-            "cc_count": ([P, I32, I32, ctypes.c_int, ctypes.c_int, U64P, DP, DP], ctypes.c_int),
-            "cc_count_per_vertex": ([P, I32, I32, ctypes.c_int, U64P, U64P], ctypes.c_int),
-            "cc_work_units": ([P, I32, I32, DP], ctypes.c_int),
-            "cc_set_timing": ([P, ctypes.c_int], ctypes.c_int),
-            "cc_get_timing": ([P, ctypes.c_char_p, DP, I64P, ctypes.c_int], ctypes.c_int),
-            "cc_reset_timing": ([P], ctypes.c_int),
-            "cc_kernel_launches": ([P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
-            "cc_count_cycle_noalloc": ([ctypes.c_int, P, ctypes.c_int, I64, P, P, P, U64P], ctypes.c_int),
-            "cc_count_batch": ([P, ctypes.POINTER(cc_request), ctypes.c_int, U64P, ctypes.POINTER(ctypes.c_int)],
-                               ctypes.c_int),
-            "cc_set_graph_capture": ([P, ctypes.c_int], ctypes.c_int),
-            "cc_autotune": ([P, I32, I32, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
-            "cc_server_create": ([ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
-            "cc_server_destroy": ([P], None),
-            "cc_server_load_csr": ([P, I64, I64P, I32P, I64, I32P], ctypes.c_int),
-            "cc_server_set_query": ([P, ctypes.c_int, ctypes.c_int, I32P, I32P], ctypes.c_int),
-            "cc_server_set_coloring_seed": ([P, U64], ctypes.c_int),
-            "cc_server_submit": ([P, I32, I32, ctypes.c_int, ctypes.c_int, U64P, I64P], ctypes.c_int),
-            "cc_server_poll": ([P, ctypes.POINTER(cc_server_result), ctypes.c_int, ctypes.c_int], ctypes.c_int),
-            "cc_server_stats": ([P, I64P, I64P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
-            "cc_strerror": ([ctypes.c_int], ctypes.c_char_p),
-        }
-        for name, (args, res) in sig.items():
-            f = getattr(L, name)
-            f.argtypes = args
-            f.restype = res
-        _lib = L
+        _lib = load_library(LIB_PATH)
     return _lib
+
+
+def variant_library(name: str):
+    """A test build of the library (see _build.VARIANTS), loaded beside libcc.so."""
+    if name not in _build.VARIANTS:
+        raise KeyError(name)
+    _build.build()
+    path = _build.variant_path(name)
+    if not os.path.exists(path):
+        raise ImportError(f"{name} is missing; build it with paper_1602_04478_gb300._build.build()")
+    return load_library(path)
 
 
 def _ptr(a, t):
@@ -154,6 +177,13 @@ def cc_set_memory_budget(h, nbytes: int) -> None:
 
 def cc_set_heavy_degree(h, degree: int) -> None:
     _check(lib().cc_set_heavy_degree(h, degree), "cc_set_heavy_degree")
+
+
+PROC_DB, PROC_PS = 0, 1
+
+
+def cc_set_procedure(h, procedure: int) -> None:
+    _check(lib().cc_set_procedure(h, procedure), "cc_set_procedure")
 
 
 def cc_load_csr(h, n: int, row_ptr: np.ndarray, col: np.ndarray) -> int:
@@ -233,6 +263,27 @@ def cc_plan_inspect(k: int, edges, block_seq=None, allow_unsupported: bool = Fal
     return blocks, aut.value
 
 
+def cc_plan_enumerate(k: int, edges):
+    """Every decomposition tree of the query (host only): list of dicts with
+    the contraction sequence (for cc_set_decomposition), whether the library
+    supports it, the paper's ranking factors and whether cc_set_query picks it."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    out = np.zeros(1 << 16, dtype=np.int32)
+    n = ctypes.c_int(0)
+    w = lib().cc_plan_enumerate(k, int(e.shape[0]), _ptr(e, ctypes.c_int32), _ptr(out, ctypes.c_int32), out.size,
+                                ctypes.byref(n))
+    if w < 0:
+        raise CCError(w, "cc_plan_enumerate")
+    plans, i = [], 0
+    while i < min(w, out.size):
+        m = int(out[i])
+        plans.append({"supported": bool(out[i + 1]), "longest": int(out[i + 2]), "boundary": int(out[i + 3]),
+                      "annotations": int(out[i + 4]), "default": bool(out[i + 5]),
+                      "seq": [int(x) for x in out[i + 6:i + 6 + m]]})
+        i += 6 + m
+    return plans
+
+
 def cc_query_info(h, qid: int):
     k, nb, lc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     aut = ctypes.c_int64()
@@ -279,6 +330,25 @@ def cc_work_units(h, gid: int, qid: int) -> float:
     u = ctypes.c_double(0)
     _check(lib().cc_work_units(h, gid, qid, ctypes.byref(u)), "cc_work_units")
     return u.value
+
+
+STAGE_KINDS = {0: "leaf", 1: "triangle", 2: "root_cycle", 3: "root_node"}
+
+
+def cc_work_detail(h, gid: int, qid: int):
+    """Per-stage structural work: list of dicts with kind, units,
+    alg_bytes and (root cycle) scans, the data edges scanned per level."""
+    cap = 64
+    kind = np.zeros(cap, dtype=np.int32)
+    units = np.zeros(cap, dtype=np.float64)
+    nbytes = np.zeros(cap, dtype=np.float64)
+    scans = np.zeros(8 * cap, dtype=np.float64)
+    n = lib().cc_work_detail(h, gid, qid, cap, _ptr(kind, ctypes.c_int32), _ptr(units, ctypes.c_double),
+                             _ptr(nbytes, ctypes.c_double), _ptr(scans, ctypes.c_double))
+    if n < 0:
+        raise CCError(n, "cc_work_detail")
+    return [{"kind": STAGE_KINDS[int(kind[i])], "units": float(units[i]), "alg_bytes": float(nbytes[i]),
+             "scans": [float(x) for x in scans[8 * i:8 * i + 8]]} for i in range(min(n, cap))]
 
 
 def cc_set_timing(h, enable: bool) -> None:

@@ -204,10 +204,14 @@ void free_pass(Ctx &c, const DevGraph &g, PassBuffers &B) {
 // status[ST_COUNT] (and d_per_vertex, rank order, when given).  No host
 // synchronisation, so a sequence of passes can be captured in a CUDA graph.
 int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers &B, u64 *status,
-                 u64 *d_per_vertex, bool count_units, double *host_units) {
+                 u64 *d_per_vertex, std::vector<StageWork> *detail) {
   const int k = p.k;
+  const bool count_units = detail != nullptr;
   int rc = CC_OK;
-  if ((rc = check(cudaMemsetAsync(status, 0, 8 * sizeof(u64), c.stream))) != CC_OK) return rc;
+  if ((rc = check(cudaMemsetAsync(status, 0, (count_units ? kStatusWords : 8) * sizeof(u64), c.stream))) != CC_OK)
+    return rc;
+  // structural counting: the device counters after the previous stage
+  u64 seen[kStatusWords] = {0};
   if ((rc = colors_fill(c, g, k, trial, B.colors)) != CC_OK) return rc;
   if (d_per_vertex && (rc = check(cudaMemsetAsync(d_per_vertex, 0, (size_t)g.n * 8, c.stream))) != CC_OK) return rc;
   Lut lut{c.lut_rank, c.lut_unrank};
@@ -220,6 +224,8 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
     bool is_root = i + 1 == p.stages.size();
     const int R = T[i].R;
     if (T[i].p && (rc = check(cudaMemsetAsync(T[i].p, 0, T[i].bytes, c.stream))) != CC_OK) break;
+    StageWork w;
+    w.kind = st.kind;
     if (st.kind == ST_LEAF) {
       LeafArgs a;
       a.g = gv;
@@ -237,8 +243,12 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
       a.R_out = R;
       a.status = status;
       if (sA + a.sY - 1 != st.s) { rc = CC_ERR_INVALID_ARG; break; }
-      // every directed edge joins one edge row with one row of the leaf's block
-      if (host_units) *host_units += (double)g.nnz * (a.E.p ? a.E.R : 1) * (a.B.p ? a.B.R : 1);
+      // every directed edge joins one edge row with one row of the leaf's
+      // block; bytes: one gathered u64 per update, the neighbour id per
+      // edge, the A rows read and the output rows written
+      w.units = (double)g.nnz * (a.E.p ? a.E.R : 1) * (a.B.p ? a.B.R : 1);
+      w.bytes = 8.0 * ((a.E.p || a.B.p) ? w.units : 0.0) + 4.0 * (double)g.nnz +
+                8.0 * (double)g.n * ((a.A.p ? a.A.R : 0) + R);
       rc = launch_leaf(c, a);
     } else if (st.kind == ST_TRI) {
       TriArgs a;
@@ -262,6 +272,9 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
       a.work_counter = B.counter;
       a.count_units = count_units;
       rc = launch_triangle(c, a);
+      // bytes (completed below from the wedge count): one neighbour id per
+      // wedge scanned, the output rows written
+      w.bytes = 8.0 * (double)(st.nb == 2 ? g.nnz : (st.nb == 1 ? g.n : 0)) * R;
     } else if (st.kind == ST_CYCLE_ROOT) {
       CycleArgs a;
       a.g = gv;
@@ -299,6 +312,14 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
       a.n_h = rho;
       for (int h = 0; h < rho; h++) a.hs[h] = h;
       a.multiplier = st.L / rho;
+      if (c.procedure == CC_PROC_PS) {
+        // PS: one split (a_0 and its opposite node), no vertex order, every
+        // match counted once with a_0's image as the source
+        a.no_order = true;
+        a.n_h = 1;
+        a.hs[0] = 0;
+        a.multiplier = 1;
+      }
       a.per_vertex = d_per_vertex;
       a.status = status;
       a.count_units = count_units;
@@ -308,8 +329,27 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
       const Table &ct = T[st.node_child[0]];
       if (ct.R != 1) { rc = CC_ERR_INVALID_ARG; break; }
       rc = launch_root_sum(c, gv, ct.p, d_per_vertex, status);
+      w.bytes = 8.0 * (double)g.n;
     } else {
       rc = CC_ERR_UNSUPPORTED;
+    }
+    if (detail && rc == CC_OK) {
+      // the device counters this stage added (the pass is not timed or captured)
+      u64 now[kStatusWords];
+      rc = check(cudaMemcpyAsync(now, status, sizeof(now), cudaMemcpyDeviceToHost, c.stream));
+      if (rc == CC_OK) rc = check(cudaStreamSynchronize(c.stream));
+      if (rc != CC_OK) break;
+      const double dev_units = (double)(now[ST_UNITS] - seen[ST_UNITS]);
+      w.units += dev_units;
+      if (st.kind == ST_TRI) w.bytes += 4.0 * dev_units;
+      if (st.kind == ST_CYCLE_ROOT) {
+        for (int j = 0; j < 8; j++) {
+          w.scans[j] = (double)(now[ST_SCAN0 + j] - seen[ST_SCAN0 + j]);
+          w.bytes += 4.0 * w.scans[j];  // one neighbour id per scanned edge
+        }
+      }
+      std::copy(now, now + kStatusWords, seen);
+      detail->push_back(w);
     }
   }
   return rc;
@@ -324,11 +364,10 @@ int status_code(const u64 *st) {
 
 // One colouring pass (plain form): allocate, enqueue, wait, read the status.
 int run_plan(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, u64 *count, bool *overflow,
-             u64 *d_per_vertex, double *units) {
+             u64 *d_per_vertex, std::vector<StageWork> *detail) {
   PassBuffers B;
   int rc = alloc_pass(c, g, p, B);
-  double host_units = 0.0;
-  if (rc == CC_OK) rc = enqueue_pass(c, g, p, trial, B, c.d_status, d_per_vertex, units != nullptr, &host_units);
+  if (rc == CC_OK) rc = enqueue_pass(c, g, p, trial, B, c.d_status, d_per_vertex, detail);
   u64 status[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (rc == CC_OK) {
     rc = check(cudaMemcpyAsync(status, c.d_status, sizeof(status), cudaMemcpyDeviceToHost, c.stream));
@@ -342,7 +381,6 @@ int run_plan(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, u64 *count, bool
   if (sc != CC_OK && sc != CC_ERR_OVERFLOW) return sc;
   *count = status[ST_COUNT];
   *overflow = sc == CC_ERR_OVERFLOW;
-  if (units) *units = host_units + (double)status[ST_UNITS];
   return CC_OK;
 }
 
@@ -376,7 +414,7 @@ int cc_create(cc_ctx **out, int device, void *cuda_stream) {
   cc_ctx *x = new cc_ctx();
   x->c.device = device;
   x->c.stream = (cudaStream_t)cuda_stream;
-  x->c.d_status = (u64 *)dev_alloc(x->c, 64);
+  x->c.d_status = (u64 *)dev_alloc(x->c, kStatusWords * sizeof(u64));
   int rc = x->c.d_status ? luts_init(x->c) : CC_ERR_OOM;
   if (rc != CC_OK) {
     cc_destroy(x);
@@ -398,7 +436,7 @@ void cc_destroy(cc_ctx *ctx) {
   batch_cache_clear(c);
   dev_free(c, c.lut_rank, 4096 * 2);
   dev_free(c, c.lut_unrank, 13 * kUnrankStride * 2);
-  dev_free(c, c.d_status, 64);
+  dev_free(c, c.d_status, kStatusWords * sizeof(u64));
   // the stream goes last: the frees above are ordered on it
   cudaStreamSynchronize(c.stream);
   if (c.own_stream) {
@@ -416,11 +454,11 @@ int cc_set_allocator(cc_ctx *ctx, cc_alloc_fn alloc, cc_free_fn free_fn, void *u
   cudaStreamSynchronize(c.stream);
   dev_free(c, c.lut_rank, 4096 * 2);
   dev_free(c, c.lut_unrank, 13 * kUnrankStride * 2);
-  dev_free(c, c.d_status, 64);
+  dev_free(c, c.d_status, kStatusWords * sizeof(u64));
   c.alloc = alloc;
   c.free_fn = free_fn;
   c.alloc_user = user;
-  c.d_status = (u64 *)dev_alloc(c, 64);
+  c.d_status = (u64 *)dev_alloc(c, kStatusWords * sizeof(u64));
   if (!c.d_status) return CC_ERR_OOM;
   return luts_init(c);
 }
@@ -429,6 +467,13 @@ int cc_set_heavy_degree(cc_ctx *ctx, int degree) {
   if (!ctx || degree < -1) return CC_ERR_INVALID_ARG;
   if (ctx->c.heavy_degree != degree) batch_cache_clear(ctx->c);
   ctx->c.heavy_degree = degree;
+  return CC_OK;
+}
+
+int cc_set_procedure(cc_ctx *ctx, int procedure) {
+  if (!ctx || (procedure != CC_PROC_DB && procedure != CC_PROC_PS)) return CC_ERR_INVALID_ARG;
+  if (ctx->c.procedure != procedure) batch_cache_clear(ctx->c);
+  ctx->c.procedure = procedure;
   return CC_OK;
 }
 
@@ -496,7 +541,7 @@ int cc_set_decomposition(cc_ctx *ctx, int32_t query_id, const int32_t *block_seq
   int rc = plan_explicit(it->second.k, it->second.edges, seq, p);
   if (rc != CC_OK) return rc;
   it->second = p;
-  for (auto &g : ctx->c.graphs) g.second.work_cache.erase(query_id);
+  for (auto &g : ctx->c.graphs) g.second.work_detail.erase(query_id);
   return CC_OK;
 }
 
@@ -534,6 +579,31 @@ int cc_plan_inspect(int k, int n_edges, const int32_t *edges, const int32_t *blo
     for (int x : kids) put(x);
   }
   if (aut) *aut = p.aut;
+  return w;
+}
+
+int cc_plan_enumerate(int k, int n_edges, const int32_t *edges, int32_t *out, int cap, int *n_plans) {
+  if (n_edges < 0 || (n_edges > 0 && !edges) || cap < 0 || (cap > 0 && !out)) return CC_ERR_INVALID_ARG;
+  std::vector<std::pair<int, int>> e;
+  for (int i = 0; i < n_edges; i++) e.push_back({edges[2 * i], edges[2 * i + 1]});
+  std::vector<PlanChoice> plans;
+  int rc = plan_enumerate(k, e, plans);
+  if (rc != CC_OK) return rc;
+  int w = 0;
+  auto put = [&](int32_t x) {
+    if (w < cap) out[w] = x;
+    w++;
+  };
+  for (auto &p : plans) {
+    put((int32_t)p.seq.size());
+    put(p.supported);
+    put(p.longest);
+    put(p.boundary);
+    put(p.annotations);
+    put(p.is_default);
+    for (int x : p.seq) put(x);
+  }
+  if (n_plans) *n_plans = (int)plans.size();
   return w;
 }
 
@@ -650,28 +720,53 @@ int cc_count_per_vertex(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int tri
   return rc;
 }
 
-int cc_work_units(cc_ctx *ctx, int32_t graph_id, int32_t query_id, double *units) {
+// Per-stage structural work of (graph, query), computed once by a counting
+// pass (the structure -- reach sets, wedges -- does not depend on the colouring).
+static int work_detail(cc_ctx *ctx, int32_t graph_id, int32_t query_id, const std::vector<StageWork> **out) {
   DevGraph *g;
   Plan *p;
   int rc = lookup(ctx, graph_id, query_id, &g, &p);
   if (rc != CC_OK) return rc;
-  if (!units) return CC_ERR_INVALID_ARG;
-  auto it = g->work_cache.find(query_id);
-  if (it != g->work_cache.end()) {
-    *units = it->second;
-    return CC_OK;
+  auto it = g->work_detail.find(query_id);
+  if (it == g->work_detail.end()) {
+    Ctx &c = ctx->c;
+    cudaSetDevice(c.device);
+    u64 cnt = 0;
+    bool ovf = false;
+    std::vector<StageWork> d;
+    rc = run_plan(c, *g, *p, 0, &cnt, &ovf, nullptr, &d);
+    if (rc != CC_OK) return rc;
+    it = g->work_detail.emplace(query_id, d).first;
   }
-  Ctx &c = ctx->c;
-  cudaSetDevice(c.device);
-  u64 cnt = 0;
-  bool ovf = false;
-  double w = 0.0;
-  // the structure (reach sets, wedges) does not depend on the colouring
-  rc = run_plan(c, *g, *p, 0, &cnt, &ovf, nullptr, &w);
+  *out = &it->second;
+  return CC_OK;
+}
+
+int cc_work_units(cc_ctx *ctx, int32_t graph_id, int32_t query_id, double *units) {
+  if (!units) return CC_ERR_INVALID_ARG;
+  const std::vector<StageWork> *d = nullptr;
+  int rc = work_detail(ctx, graph_id, query_id, &d);
   if (rc != CC_OK) return rc;
-  g->work_cache[query_id] = w;
+  double w = 0.0;
+  for (auto &s : *d) w += s.units;
   *units = w;
   return CC_OK;
+}
+
+int cc_work_detail(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int cap, int32_t *kind, double *units,
+                   double *alg_bytes, double *scans) {
+  if (cap < 0) return CC_ERR_INVALID_ARG;
+  const std::vector<StageWork> *d = nullptr;
+  int rc = work_detail(ctx, graph_id, query_id, &d);
+  if (rc != CC_OK) return rc;
+  for (int i = 0; i < cap && i < (int)d->size(); i++) {
+    const StageWork &s = (*d)[i];
+    if (kind) kind[i] = s.kind;
+    if (units) units[i] = s.units;
+    if (alg_bytes) alg_bytes[i] = s.bytes;
+    if (scans) std::copy(s.scans, s.scans + 8, scans + 8 * i);
+  }
+  return (int)d->size();
 }
 
 int cc_set_timing(cc_ctx *ctx, int enable) {

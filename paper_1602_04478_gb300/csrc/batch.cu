@@ -69,7 +69,7 @@ static int enqueue_batch(Ctx &c, const cc_request *reqs, int n, Ctx::BatchCache 
     c.cur_tuned_heavy = g.tuned_heavy.count(reqs[i].query_id) ? g.tuned_heavy[reqs[i].query_id] : -1;
     for (int t = 0; t < reqs[i].trials; t++, slot++) {
       int rc = enqueue_pass(c, g, p, (int64_t)reqs[i].first_trial + t, b.bufs[i], b.results + slot * 8, nullptr,
-                            false, nullptr);
+                            nullptr);
       if (rc != CC_OK) return rc;
     }
   }

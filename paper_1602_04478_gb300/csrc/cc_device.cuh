@@ -82,10 +82,26 @@ __device__ __forceinline__ unsigned long long warp_sum_ck(unsigned long long v, 
 }
 
 // status words in device memory
-enum { ST_COUNT = 0, ST_OVERFLOW = 1, ST_TIMEOUT = 2, ST_BADGRAPH = 3, ST_UNITS = 4 };
+// ST_SCAN0 + j: data edges scanned out of level j of a root cycle's halves
+// (structural counting only; a status block then has kStatusWords words)
+enum { ST_COUNT = 0, ST_OVERFLOW = 1, ST_TIMEOUT = 2, ST_BADGRAPH = 3, ST_UNITS = 4, ST_MAXDEG = 5, ST_SCAN0 = 8 };
+constexpr int kStatusWords = 16;
 
 __device__ __forceinline__ void flag_overflow(unsigned long long *status, unsigned ovf) {
   if (ovf) atomicOr(status + ST_OVERFLOW, 1ull);
+}
+
+// True, in every thread of the block, when a count of this pass has already
+// exceeded 2^64-1.  The uint64 result is then fixed (UINT64_MAX with
+// CC_ERR_OVERFLOW), so the work kernels of the general root-cycle path
+// return at once; the kernels that return their scratch to zero still run.
+// The flag is read once per block, so the decision is uniform: call it at
+// kernel entry, before any divergence, in a 1-D block.
+__device__ __forceinline__ bool block_sees_overflow(const unsigned long long *status) {
+  __shared__ int s_flag;
+  if (threadIdx.x == 0) s_flag = *(const volatile unsigned long long *)(status + ST_OVERFLOW) != 0ull;
+  __syncthreads();
+  return s_flag != 0;
 }
 
 // first index in sorted a[lo, hi) with a[i] >= key

@@ -48,6 +48,25 @@ int plan_explicit(int k, const std::vector<std::pair<int, int>> &edges,
                   const std::vector<int> &block_seq, Plan &out);
 int64_t count_automorphisms(int k, const std::vector<std::pair<int, int>> &edges);
 
+// One decomposition tree: its contraction sequence (cc_set_decomposition's
+// block_seq) and the paper's ranking factors (Section 5.3).
+struct PlanChoice {
+  std::vector<int> seq;
+  bool supported = false, is_default = false;
+  int longest = 0, boundary = 0, annotations = 0;
+};
+int plan_enumerate(int k, const std::vector<std::pair<int, int>> &edges, std::vector<PlanChoice> &out);
+
+// Structural work of one stage of a colouring pass (independent of the
+// colouring): edge-subset updates, algorithmic bytes (the compulsory reads
+// and writes of its kernels) and, for a root cycle, the data edges scanned
+// out of each level (both halves).
+struct StageWork {
+  int kind = 0;
+  double units = 0, bytes = 0;
+  double scans[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
 // ------------------------------- data graph -------------------------------
 struct DevGraph {
   bool owned = true;          // false: device arrays belong to another context (shared graph)
@@ -62,7 +81,7 @@ struct DevGraph {
   int colors_T = 0;
   int colors_max = -1;        // largest explicit colour (must be below the query's k)
   std::vector<int64_t> h_row;  // host copy of the relabelled row pointers
-  std::map<int, double> work_cache;  // query id -> structural work units
+  std::map<int, std::vector<struct StageWork>> work_detail;  // query id -> per-stage structural work
   std::map<int, int> tuned_heavy;    // query id -> heavy-source degree threshold (autotuned)
   std::vector<int64_t> h_push_work;  // per rank u: pairs (v, w), v in N<(u), w in N(v), w < u (empty: not yet)
 };
@@ -96,6 +115,7 @@ struct Ctx {
   const int64_t *cur_graph_row = nullptr;  // host row pointers of the graph being counted
   DevGraph *cur_graph = nullptr;           // the graph being counted
   int heavy_degree = -1;         // sources of at least this degree take the heavy path (-1: tuned / default)
+  int procedure = CC_PROC_DB;    // root cycles of length >= 4: DB (degree order) or PS (no order)
   int cur_tuned_heavy = -1;      // tuned threshold of the (graph, query) being enqueued, -1 none
   cudaStream_t own_stream = nullptr;  // created for graph capture when the caller's stream is the legacy one
   bool capture = true;           // batches replay a captured CUDA graph

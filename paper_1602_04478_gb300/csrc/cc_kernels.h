@@ -81,6 +81,7 @@ struct CycleArgs {
   u64 *status = nullptr;
   bool count_units = false;   // add the structural edge-subset work to status[ST_UNITS]
   int32_t light_end = 0;      // the per-CTA kernel takes sources of rank < light_end
+  bool no_order = false;      // PS procedure: paths from u are not restricted to vertices below u
 };
 int run_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank, int B);
 bool plain_cycle_eligible(const CycleArgs &a);
@@ -114,11 +115,14 @@ struct PassBuffers {
 int alloc_pass(Ctx &c, const DevGraph &g, const Plan &p, PassBuffers &B);
 size_t request_table_bytes(const Plan &p, const DevGraph &g);
 void free_pass(Ctx &c, const DevGraph &g, PassBuffers &B);
+// detail (nullable): structural counting pass; per-stage work appended (the
+// pass synchronises after every stage and needs a status block of
+// kStatusWords words)
 int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers &B, u64 *status, u64 *d_per_vertex,
-                 bool count_units, double *host_units);
+                 std::vector<StageWork> *detail);
 int status_code(const u64 *st);
 int run_plan(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, u64 *count, bool *overflow, u64 *d_per_vertex,
-             double *units);
+             std::vector<StageWork> *detail);
 
 int graph_load(Ctx &c, int64_t n, const int64_t *row_ptr, const int32_t *col, int64_t nnz, DevGraph &g);
 void graph_free(Ctx &c, DevGraph &g);

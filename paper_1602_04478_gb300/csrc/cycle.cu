@@ -90,6 +90,12 @@ __device__ __host__ inline void level_info(const CycleArgs &a, int h, int half, 
   }
 }
 
+// End of the part of v's row a path from source u may extend into: the
+// vertices below u (DB, rows are rank ordered), or the whole row (PS).
+__device__ __forceinline__ int64_t row_end(const CycleArgs &a, int64_t vb, int32_t v, int32_t u) {
+  return a.no_order ? a.g.row[v + 1] : lower_bound_i32(a.g.col, vb, a.g.row[v + 1], u);
+}
+
 __device__ __forceinline__ int rows_of(int k, int s) {
   // C(k-2, s-2) for the pair rows
   int n = k - 2, r = s - 2;
@@ -213,7 +219,10 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
   const int rp = L / 2, rm = L - L / 2;
   while (true) {
     if (tid == 0) {
-      s_u = (int)(a.light_end - 1 - atomicAdd(work_counter, 1));
+      // once a count of this pass has exceeded 2^64-1 the result is fixed
+      // (UINT64_MAX, CC_ERR_OVERFLOW): take no further source
+      const bool done = *(const volatile unsigned long long *)(a.status + ST_OVERFLOW) != 0ull;
+      s_u = done ? -1 : (int)(a.light_end - 1 - atomicAdd(work_counter, 1));
       s_total = 0;
       s_ovf = 0;
     }
@@ -221,7 +230,8 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
     const int32_t u = s_u;
     if (u < 0) break;
     const int64_t ub = a.g.row[u];
-    const int du = a.g.lo_cnt[u];
+    // DB: the lower neighbours (a row prefix); PS: every neighbour
+    const int du = a.no_order ? (int)(a.g.row[u + 1] - ub) : a.g.lo_cnt[u];
     const int cu = a.colors[u];
     if (du >= 2) {
       for (int hi = 0; hi < a.n_h; hi++) {
@@ -280,6 +290,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
           // extension out of level 0 for both halves: du edges times the start row's slots
           u64 r0 = 1 + (u64)(a.N[h].p ? a.N[h].R : 1);
           atomicAdd(a.status + ST_UNITS, (u64)du * r0);
+          atomicAdd(a.status + ST_SCAN0, 2ull * (u64)du);
         }
         __syncthreads();
         // node joins at level 1
@@ -313,7 +324,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
               const int cv = a.colors[v];
               const u64 *src = P.rows[hf][j] + (int64_t)v * sc.rstride[hf][j];
               const int64_t vb = a.g.row[v];
-              const int64_t ve = lower_bound_i32(a.g.col, vb, a.g.row[v + 1], u);
+              const int64_t ve = row_end(a, vb, v, u);
               for (int64_t e = vb + lane; e < ve; e += 32) {
                 const int32_t w = __ldg(a.g.col + e);
                 if (stamp_set(P.stamp, w, cur, hf * kMaxLevels + j + 1)) {
@@ -352,13 +363,16 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
               level_info(a, h, hf, j, lj, nullptr);
               const u64 Rj = (u64)rows_of(k, lj.s);
               const int cnt = s_cnt[hsl * kMaxLevels + j];
-              u64 acc = 0;
+              u64 acc = 0, edges = 0;
               for (int i = tid; i < cnt; i += kCtaThreads) {
                 const int32_t v = P.list[hsl][j][i];
                 const int64_t vb = a.g.row[v];
-                acc += (u64)(lower_bound_i32(a.g.col, vb, a.g.row[v + 1], u) - vb) * Rj;
+                const u64 e = (u64)(row_end(a, vb, v, u) - vb);
+                acc += e * Rj;
+                edges += e;
               }
               if (acc) atomicAdd(a.status + ST_UNITS, acc);
+              if (edges && j < 8) atomicAdd(a.status + ST_SCAN0 + j, edges);
             }
           }
         }
@@ -377,7 +391,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
           for (int i = wib; i < cnt; i += kWarps) {
             const int32_t v = P.list[hf][lv][i];
             const int64_t vb = a.g.row[v];
-            const int64_t ve = lower_bound_i32(a.g.col, vb, a.g.row[v + 1], u);
+            const int64_t ve = row_end(a, vb, v, u);
             for (int64_t e = vb + lane; e < ve; e += 32) {
               const int32_t x = __ldg(a.g.col + e);
               if (stamp_set(P.stamp, x, cur, 2 * kMaxLevels)) {
@@ -408,7 +422,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
             __syncwarp();
             if (cx != cu) {
               const int64_t xb = a.g.row[x];
-              const int64_t xe = lower_bound_i32(a.g.col, xb, a.g.row[x + 1], u);
+              const int64_t xe = row_end(a, xb, x, u);
               for (int64_t e = xb + lane; e < xe; e += 32) {
                 const int32_t w = __ldg(a.g.col + e);
                 const int cw = a.colors[w];
@@ -558,7 +572,8 @@ int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   // sources of degree >= heavy_degree go to the grouped heavy path
   const int64_t n = a.g.n;
   int hd = c.heavy_degree >= 0 ? c.heavy_degree : (c.cur_tuned_heavy >= 0 ? c.cur_tuned_heavy : 256);
-  if (a.count_units) hd = 1 << 30;  // structural counting runs on the per-CTA path only
+  // structural counting and the PS procedure run on the per-CTA path only
+  if (a.count_units || a.no_order) hd = 1 << 30;
   int64_t lo = 0, hi = n;
   while (lo < hi) {
     int64_t mid = (lo + hi) / 2;
@@ -568,7 +583,7 @@ int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   a.light_end = (int32_t)lo;
   // plain C4..C6: 16-bit level-2 rows on the heavy path need max degree < 2^16
   // the plain kernels keep 16-bit row entries (degree < 2^16) and tag neighbours with their colour (n < 2^29)
-  const bool plain = plain_cycle_eligible(a) && !a.count_units && (c.cur_graph_row[n] - c.cur_graph_row[n - 1]) < 65536 &&
+  const bool plain = plain_cycle_eligible(a) && !a.count_units && !a.no_order && (c.cur_graph_row[n] - c.cur_graph_row[n - 1]) < 65536 &&
                      n < ((int64_t)1 << 29);
   if (a.light_end < n) {
     int rc = plain ? run_plain_heavy(c, a, a.light_end) : run_heavy(c, a, a.light_end, heavy_group_size(a));

@@ -111,6 +111,7 @@ __device__ __forceinline__ bool hv_stamp_set(unsigned long long *stamp, int32_t 
 
 // -------------------------------- level 1 --------------------------------
 __global__ void k_hv_level1(CycleArgs a, HvScratch S, HvGroup G, int h) {
+  if (block_sees_overflow(a.status)) return;  // the result is already UINT64_MAX
   const int64_t n = a.g.n;
   unsigned ovf = 0;
   for (int b = blockIdx.y; b < G.B; b += gridDim.y) {
@@ -161,6 +162,7 @@ __global__ void k_hv_level1(CycleArgs a, HvScratch S, HvGroup G, int h) {
 
 // ------------------------------- node joins -------------------------------
 __global__ void k_hv_join(CycleArgs a, HvScratch S, HvGroup G, int h, int hf, int j) {
+  if (block_sees_overflow(a.status)) return;  // the result is already UINT64_MAX
   const int64_t n = a.g.n;
   HvLevelInfo li;
   hv_level(a, h, hf, j, li);
@@ -198,6 +200,7 @@ __global__ void k_hv_join(CycleArgs a, HvScratch S, HvGroup G, int h, int hf, in
 
 // --------------------------------- pushes ---------------------------------
 __global__ void k_hv_push(CycleArgs a, HvScratch S, HvGroup G, int h, int hf, int j) {
+  if (block_sees_overflow(a.status)) return;  // the result is already UINT64_MAX
   const int64_t n = a.g.n;
   HvLevelInfo lj, ln;
   hv_level(a, h, hf, j, lj);
@@ -360,6 +363,7 @@ __device__ __forceinline__ void hv_gather(const CycleArgs &a, const HvScratch &S
 
 __global__ void __launch_bounds__(kHvThreads) k_hv_pull(CycleArgs a, HvScratch S, HvGroup G, int h,
                                                         int32_t x_split) {
+  if (block_sees_overflow(a.status)) return;  // the result is already UINT64_MAX
   extern __shared__ u64 hv_acc[];
   const int tid = threadIdx.x, lane = tid & 31;
   const int stride = S.accP + (S.same_acc ? 0 : S.accM);

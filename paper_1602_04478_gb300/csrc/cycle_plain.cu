@@ -620,7 +620,15 @@ __device__ __forceinline__ int pair_idx(int a, int b) {
   return hi * (hi - 1) / 2 + lo;
 }
 
+#ifdef CC_TEST_WAIT_EXPIRES
+// Test build (libcc_waittest.so) only: every thread that finds v already
+// claimed enters the wait as if the claimant had not published yet, and the
+// wait gives up at once, so the report of a wait that ran out reaches the
+// caller deterministically.  No access changes: the contribution is skipped.
+constexpr int kPlSpinLimit = 0;
+#else
 constexpr int kPlSpinLimit = 1 << 22;
+#endif
 
 // Local index of v at one level: claimed (and listed) by the first thread to
 // reach it, read by the others; -1 when the wait for the claimant gave up.
@@ -632,6 +640,9 @@ __device__ __forceinline__ int pl_index(int32_t *id, int32_t v, int32_t *list, i
     atomicExch(id + v, i + 1);
     return i;
   }
+#ifdef CC_TEST_WAIT_EXPIRES
+  old = -1;
+#endif
   for (int spins = 0; old < 0; spins++) {
     if (spins == kPlSpinLimit) {
       tmo = 1u;

@@ -50,7 +50,7 @@ __global__ void k_na_prepare(int64_t n, const int64_t *row, const int32_t *col, 
                              int32_t *lo_cnt, u64 *status) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = row[v], e = row[v + 1];
-    atomicMax(status + 5, (u64)(e > b ? e - b : 0));
+    atomicMax(status + ST_MAXDEG, (u64)(e > b ? e - b : 0));
     bool bad = e < b || colors[v] >= k;
     int32_t lo = 0;
     for (int64_t i = b; i < e && !bad; i++) {
@@ -117,7 +117,7 @@ extern "C" int cc_count_cycle_noalloc(int device, void *cuda_stream, int L, int6
       cudaStreamSynchronize(st) != cudaSuccess)
     return CC_ERR_CUDA;
   if (pre[ST_BADGRAPH]) return CC_ERR_BAD_GRAPH;
-  if (pre[5] >= 65536) return CC_ERR_INVALID_ARG;
+  if (pre[ST_MAXDEG] >= 65536) return CC_ERR_INVALID_ARG;
   GraphView g;
   g.n = n;
   g.row = d_row_ptr;
@@ -130,6 +130,8 @@ extern "C" int cc_count_cycle_noalloc(int device, void *cuda_stream, int L, int6
       cudaStreamSynchronize(st) != cudaSuccess)
     return CC_ERR_CUDA;
   if (h[ST_BADGRAPH]) return CC_ERR_BAD_GRAPH;
+  // a bounded wait that gave up skipped a contribution: the count is incomplete
+  if (h[ST_TIMEOUT]) return CC_ERR_TIMEOUT;
   if (h[ST_OVERFLOW]) {
     *count = UINT64_MAX;
     return CC_ERR_OVERFLOW;

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cstring>
 #include <functional>
+#include <map>
 
 #include "cc_internal.h"
 
@@ -393,6 +394,70 @@ int plan_query(int k, const std::vector<std::pair<int, int>> &edges, Plan &out) 
   out.stages = best_st;
   finish(out, k, edges);
   return out.supported ? CC_OK : CC_ERR_UNSUPPORTED;
+}
+
+// Every decomposition tree of the query (Section 5.3: one tree per sequence
+// of choices; sequences that differ only in the order of independent
+// contractions give the same tree, kept once by the root block's structural
+// signature), each as the contraction sequence cc_set_decomposition takes,
+// with the paper's ranking factors.
+int plan_enumerate(int k, const std::vector<std::pair<int, int>> &edges, std::vector<PlanChoice> &out) {
+  int rc = validate(k, edges);
+  if (rc != CC_OK) return rc;
+  Plan def;
+  int drc = plan_query(k, edges, def);
+  const std::string def_sig = (drc == CC_OK || drc == CC_ERR_UNSUPPORTED) && !def.stages.empty()
+                                  ? def.stages.back().sig : std::string();
+  QS s0;
+  init_state(s0, k, edges);
+  std::map<std::string, size_t> seen;
+  int explored = 0;
+  const int kCap = 20000;
+  std::function<void(QS &, std::vector<Stage> &)> dfs = [&](QS &s, std::vector<Stage> &st) {
+    if (explored >= kCap) return;
+    bool ok = true;
+    size_t mark = st.size();
+    QS saved = s;
+    if (try_root(s, st, &ok)) {
+      if (ok) {
+        explored++;
+        Plan p;
+        p.stages = st;
+        finish(p, k, edges);
+        const std::string &sig = p.stages.back().sig;
+        if (!seen.count(sig)) {
+          PlanChoice c;
+          for (size_t i = 0; i + 1 < p.stages.size(); i++) {
+            const Stage &g = p.stages[i];
+            c.seq.push_back(g.kind == ST_LEAF ? 0 : g.L);
+            for (int j = 0; j < g.L; j++) c.seq.push_back(g.nodes[j]);
+          }
+          Score sc = score_of(p.stages);
+          c.supported = sc.unsupported == 0;
+          c.longest = sc.longest;
+          c.boundary = sc.boundary;
+          c.annotations = sc.annotations;
+          c.is_default = sig == def_sig;
+          seen[sig] = out.size();
+          out.push_back(c);
+        }
+      }
+      st.resize(mark);
+      s = saved;
+      return;
+    }
+    std::vector<Cand> cs = candidates(s);
+    for (auto &c : cs) {
+      QS t = s;
+      apply(t, c, st, false);
+      dfs(t, st);
+      st.resize(mark);
+      if (explored >= kCap) return;
+    }
+  };
+  std::vector<Stage> st;
+  dfs(s0, st);
+  return out.empty() ? CC_ERR_NOT_TW2 : CC_OK;
 }
 
 int plan_explicit(int k, const std::vector<std::pair<int, int>> &edges,

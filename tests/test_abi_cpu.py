@@ -39,3 +39,14 @@ def test_error_table_matches_header():
     src = open(os.path.join(ROOT, "include", "cc.h")).read()
     codes = dict((int(v), k) for k, v in re.findall(r"#define (CC_ERR_[A-Z0-9_]+) \((-?\d+)\)", src))
     assert codes == P.ERRORS
+
+
+def test_test_builds_export_the_same_symbols():
+    # the test variants (same sources, one compile-time switch) keep the boundary
+    from paper_1602_04478_gb300 import _build
+    P.build()
+    for name in _build.VARIANTS:
+        path = _build.variant_path(name)
+        out = subprocess.check_output(["nm", "-D", "--defined-only", path]).decode()
+        exported = set(line.split()[-1] for line in out.splitlines() if " T " in line)
+        assert not [n for n in declared_functions() if n not in exported], name

@@ -2,7 +2,10 @@
 exponent 2.1) in the configuration bench.py times.
 
 * C6: the count split by highest cycle vertex; sampled sources are checked
-  one by one against the oracle restricted to those sources.
+  one by one against the oracle restricted to those sources, live for
+  sources of low and medium degree and from stored oracle values
+  (tests/golden/cl1e6.txt, written by tests/golden/make_golden.py) for hub
+  sources of degree 256 to 4,202, which take the grouped heavy path.
 * C5 (the batched configuration's cycle query): sampled sources, as for C6.
 * glasses and the 4-cycle with a chord and a pendant: the oracle cannot
   build their tables over the whole graph in test time, so properties that
@@ -12,6 +15,7 @@ exponent 2.1) in the configuration bench.py times.
 import numpy as np
 import pytest
 
+import golden_io
 import graphgen as gg
 import oracle as O
 
@@ -51,7 +55,19 @@ def test_c6_sampled_sources_match_oracle(big):
     _, _, per = O.dp_count(g, k, e, O.colors(1, 0, g.n, k), root_filter=filt, per_source=True)
     for v in pick:
         assert int(pv[v]) == per[v], int(v)
+    # hub sources (grouped heavy path): stored oracle values
+    gold = golden_io.load("cl1e6")
+    assert golden_io.fingerprint(g) == gold.graph_sha["cl1e6"]
+    hubs = gold.sources[("cl1e6", "C6", 1, 0)]
+    assert len(hubs) >= 24 and max(deg[v] for v in hubs) == deg.max()
+    for v, want in hubs.items():
+        assert int(pv[v]) == want, (int(v), int(deg[v]))
+    # the same sources at the library's own threshold
     P.cc_set_heavy_degree(ctx.h, -1)
+    pv2, total2 = ctx.count_per_vertex(gid, qid, 0)
+    assert total2 == total
+    for v, want in hubs.items():
+        assert int(pv2[v]) == want, (int(v), int(deg[v]))
 
 
 def test_c5_sampled_sources_match_oracle(big):
@@ -70,6 +86,9 @@ def test_c5_sampled_sources_match_oracle(big):
     _, _, per = O.dp_count(g, k, e, O.colors(3, 0, g.n, k), root_filter=filt, per_source=True)
     for v in pick:
         assert int(pv[v]) == per[v], int(v)
+    gold = golden_io.load("cl1e6")
+    for v, want in gold.sources[("cl1e6", "C5", 3, 0)].items():
+        assert int(pv[v]) == want, (int(v), int(deg[v]))
 
 
 def test_chord_pendant_decomposition_invariant_at_full_size(big):

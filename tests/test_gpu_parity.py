@@ -9,6 +9,7 @@ import math
 import numpy as np
 import pytest
 
+import golden_io
 import graphgen as gg
 import oracle as O
 
@@ -70,8 +71,13 @@ def gpu_count(cc, g, gid, k, edges, seed, trials):
 def test_count_matches_oracle(cc, gname, qname):
     g = graph(gname)
     k, e = QUERIES[qname]
+    # queries with k >= 7 on the larger graphs: the oracle's values are stored
+    # (tests/golden/k7plus.txt, written by tests/golden/make_golden.py)
+    stored = None
     if gname != "er60" and k >= 7:
-        pytest.skip("k >= 7 runs on the 60-vertex graph (oracle time); larger graphs cover k <= 6")
+        gold = golden_io.load("k7plus")
+        assert golden_io.fingerprint(g) == gold.graph_sha[gname]
+        stored = gold.counts
     gid = cc.load_graph(g)
     try:
         seed = 7
@@ -79,8 +85,10 @@ def test_count_matches_oracle(cc, gname, qname):
         col, est, aut, qid = gpu_count(cc, g, gid, k, e, seed, trials)
         assert aut == O.automorphisms(k, e)
         for t in range(trials):
-            cols = O.colors(seed, t, g.n, k)
-            expect, ovf = O.dp_count(g, k, e, cols)
+            if stored is not None:
+                expect, ovf = stored[(gname, qname, seed, t)]
+            else:
+                expect, ovf = O.dp_count(g, k, e, O.colors(seed, t, g.n, k))
             assert not ovf
             assert int(col[t]) == expect, (qname, gname, t)
             scale = k ** k / math.factorial(k) / aut
@@ -116,11 +124,7 @@ def _wheel_with_chords():
     # a hub adjacent to all 9000 other vertices (more lower neighbours than
     # the shared-memory hash holds: the CTA kernel scans it by binary search),
     # a ring through them and random chords (many hashed sources of degree >= 32)
-    rng = np.random.default_rng(11)
-    n = 9001
-    e = [(0, i) for i in range(1, n)] + [(i, i % 9000 + 1) for i in range(1, n)]
-    e += [tuple(x) for x in rng.integers(1, n, size=(30000, 2)) if x[0] != x[1]]
-    return gg.from_edges(n, np.array(e))
+    return gg.wheel_with_chords()
 
 
 @pytest.mark.parametrize("qname", ["triangle", "diamond", "chord_pendant", "tailed_triangle", "bowtie"])
@@ -138,6 +142,25 @@ def test_triangle_sources_of_every_degree(cc, qname):
         expect, _, per = O.dp_count(g, k, e, O.colors(5, 0, g.n, k), per_source=True)
         assert total == expect
         assert [int(x) for x in pv] == per
+    finally:
+        cc.free_graph(gid)
+
+
+@pytest.mark.parametrize("qname", ["glasses", "C5_pendant_path", "C6_2pendants", "C7"])
+def test_large_queries_on_the_wheel(cc, qname):
+    # the benchmark's glasses and the doubly annotated cycles on a graph whose
+    # triangle blocks reach the hashed hub kernel and the hub above the hash
+    # capacity; stored oracle values (tests/golden/k7plus.txt)
+    import paper_1602_04478_gb300 as P
+    gold = golden_io.load("k7plus")
+    g = gold.graph("wheel")
+    k, e = QUERIES[qname]
+    gid = cc.load_graph(g)
+    try:
+        P.cc_set_coloring_seed(cc.h, 5)
+        qid = cc.set_query(k, e)
+        got = int(cc.count(gid, qid, 0, 1)[0][0])
+        assert got == gold.counts[("wheel", qname, 5, 0)][0]
     finally:
         cc.free_graph(gid)
 

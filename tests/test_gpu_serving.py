@@ -1,15 +1,17 @@
 """Serving loop: continuous batching with admission by table memory.
 
-Each request's counts must be the same alone (a plain cc_count on its own
-context, same seed) and in the mix (served concurrently with others), and the
-server must actually run requests side by side while keeping the memory it
-admits within the budget.
+Each request's counts must equal the oracle's (stored values,
+tests/golden/serving.txt, written by tests/golden/make_golden.py) and be the
+same alone (a plain cc_count on its own context, same seed) and in the mix
+(served concurrently with others); the server must actually run requests side
+by side while keeping the memory it admits within the budget.
 """
 import time
 
 import numpy as np
 import pytest
 
+import golden_io
 import graphgen as gg
 
 pytestmark = pytest.mark.gpu
@@ -23,8 +25,12 @@ def env():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_1602_04478_gb300 as P
-    graphs = [gg.chung_lu(3000, 8, 2.1, 3), gg.erdos_renyi(2000, 10000, 1), gg.chung_lu(20000, 12, 2.3, 4)]
-    return P, graphs
+    gold = golden_io.load("serving")
+    graphs = [gold.graph(name) for name in GRAPH_NAMES]
+    return P, graphs, gold
+
+
+GRAPH_NAMES = ["cl3000", "er2000", "cl20000"]
 
 
 def _alone(P, g, k, e, seed, t0, T):
@@ -53,25 +59,24 @@ def _serve_all(srv, reqs, timeout_s=300):
 
 
 def test_results_same_alone_and_in_mix(env):
-    P, graphs = env
+    P, graphs, gold = env
     srv = P.Server(0, workers=4)
     try:
         srv.set_seed(21)
         gids = [srv.load_graph(g) for g in graphs]
         qids = {name: srv.set_query(*gg.query(name)) for name in QUERIES}
-        rng = np.random.default_rng(5)
         reqs = []
-        for i in range(36):
-            gi = int(rng.integers(len(graphs)))
-            qn = QUERIES[int(rng.integers(len(QUERIES)))]
-            reqs.append((gids[gi], qids[qn], int(rng.integers(0, 5)), int(rng.integers(1, 4)), gi, qn))
+        for gname, qn, t0, T in gold.requests:
+            gi = GRAPH_NAMES.index(gname)
+            reqs.append((gids[gi], qids[qn], t0, T, gi, qn))
         out = _serve_all(srv, [r[:4] for r in reqs])
         for i, (gid, qid, t0, T, gi, qn) in enumerate(reqs):
             k, e = gg.query(qn)
-            want = _alone(P, graphs[gi], k, e, 21, t0, T)
             got = [int(x) for x in out[i]["colorful"]]
-            assert got == want, (i, qn, gi)
-            assert out[i]["status"] in (0, -6)
+            oracle = [gold.counts[(GRAPH_NAMES[gi], qn, 21, t)][0] for t in range(t0, t0 + T)]
+            assert got == oracle, (i, qn, gi)
+            assert got == _alone(P, graphs[gi], k, e, 21, t0, T), (i, qn, gi)
+            assert out[i]["status"] == 0
         # work of different requests overlapped on the device
         iv = sorted((r["admit_s"], r["done_s"]) for r in out.values())
         overlap = max(sum(1 for a, b in iv if a <= t < b) for t, _ in iv)
@@ -81,7 +86,7 @@ def test_results_same_alone_and_in_mix(env):
 
 
 def test_admission_respects_memory_budget(env):
-    P, graphs = env
+    P, graphs, gold = env
     g = graphs[2]
     # edge-keyed table of chord_pendant on this graph: nnz x 3 x 8 bytes, plus colours
     need = g.nnz * 3 * 8 + g.n + 256
@@ -98,6 +103,7 @@ def test_admission_respects_memory_budget(env):
         k, e = gg.query("chord_pendant")
         for i in range(6):
             assert [int(x) for x in out[i]["colorful"]] == _alone(P, g, k, e, 3, i, 1)
+            assert int(out[i]["colorful"][0]) == gold.counts[("cl20000", "chord_pendant", 3, i)][0]
         # a request that alone exceeds the budget is refused at submission
         big = srv.set_query(*gg.query("diamond"))
         small = P.Server(0, workers=1, memory_budget=1 << 20)
@@ -115,7 +121,7 @@ def test_admission_respects_memory_budget(env):
 
 
 def test_requests_arriving_while_others_run_are_admitted(env):
-    P, graphs = env
+    P, graphs, gold = env
     srv = P.Server(0, workers=3)
     try:
         srv.set_seed(9)
@@ -140,7 +146,10 @@ def test_requests_arriving_while_others_run_are_admitted(env):
         k, e = gg.query("C4")
         for i, t in enumerate(late):
             assert [int(x) for x in res[t]["colorful"]] == _alone(P, graphs[0], k, e, 9, 10 + i, 1)
+            assert int(res[t]["colorful"][0]) == gold.counts[("cl3000", "C4", 9, 10 + i)][0]
         k6, e6 = gg.query("C6")
-        assert [int(x) for x in res[long_t]["colorful"]] == _alone(P, graphs[2], k6, e6, 9, 0, 24)
+        got = [int(x) for x in res[long_t]["colorful"]]
+        assert got == _alone(P, graphs[2], k6, e6, 9, 0, 24)
+        assert got == [gold.counts[("cl20000", "C6", 9, t)][0] for t in range(24)]
     finally:
         srv.close()

@@ -350,3 +350,38 @@ def test_overflow_is_reported_not_wrapped():
     assert expect > 2**64
     got, ovf = O.dp_count(g, k, e, col)
     assert ovf and got == expect
+
+
+# ------------------------- structural work counter -------------------------
+@pytest.mark.parametrize("L", [4, 5, 6])
+def test_cycle_scans_complete_graph_closed_form(L):
+    # In K_n every vertex has degree n-1, so the degree order is the id order.
+    # A source u (u >= 2 lower neighbours) scans u edges out of level 0 per
+    # half; level 1 is {0..u-1}, each of whose members has u-1 neighbours
+    # below u; level 2 is again {0..u-1}.  Slots per level j: 1, then
+    # C(k-2, j-1) (Section 5: high-starting paths, signatures holding chi(u)
+    # and the end's colour).
+    n = 30
+    g = gg.complete_graph(n)
+    k = L
+    depths = [L // 2, L - L // 2]
+    scans = [0] * 8
+    units = 0
+    for u in range(2, n):
+        for d in depths:
+            per_level = [u] + [u * (u - 1)] * (d - 1)
+            for j, e in enumerate(per_level):
+                scans[j] += e
+                units += e * (1 if j == 0 else math.comb(k - 2, j - 1))
+    tot, sc = O.cycle_units(g, L, k, scans=True)
+    assert sc == [float(x) for x in scans]
+    assert tot == units
+
+
+def test_cycle_scans_star_graph():
+    # a star: only the centre has lower neighbours; its leaves have none below it
+    n = 50
+    g = gg.from_edges(n, [(0, i) for i in range(1, n)])
+    tot, sc = O.cycle_units(g, 6, 6, scans=True)
+    assert sc == [2.0 * (n - 1)] + [0.0] * 7
+    assert tot == 2.0 * (n - 1)

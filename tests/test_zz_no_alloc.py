@@ -3,8 +3,8 @@
 Callers that cannot let a library allocate GPU memory (a fixed device arena,
 no cudaMalloc allowed) use cc_count_cycle_noalloc: they pass device buffers
 for the graph and the colours, and the library works in its own static
-device array.  Its counts must equal cc_count's (the allocating path) for
-the same graph, colours and query, call after call.
+device array.  Its counts must equal cc_count's (the allocating path) and the
+oracle's for the same graph, colours and query, call after call.
 """
 import numpy as np
 import pytest
@@ -54,6 +54,7 @@ def test_noalloc_matches_allocating_path(env, gname, graph, L):
             got = P.cc_count_cycle_noalloc(0, stream, L, g.n, rp.data_ptr(), col.data_ptr(), c.data_ptr())
             torch.cuda.synchronize()
             assert got == expect, (gname, L, trial, got, expect)
+            assert got == O.dp_count(g, k, e, colors)[0], (gname, L, trial)
     finally:
         ctx.free_graph(gid)
 
@@ -79,3 +80,34 @@ def test_noalloc_rejects_bad_inputs(env):
     assert P.ERRORS[ei.value.code] == "CC_ERR_BAD_GRAPH"
     with pytest.raises(P.CCError):
         P.cc_count_cycle_noalloc(0, None, 7, g.n, rp.data_ptr(), col.data_ptr(), c.data_ptr())
+
+
+def _hub_and_clique(hub_degree):
+    # vertex 0 adjacent to vertices 1..hub_degree; vertices 1..48 also form a
+    # clique, so every cycle through the hub runs through the clique and the
+    # hub's row is the longest the kernel reads
+    e = [(0, i) for i in range(1, hub_degree + 1)]
+    e += [(a, b) for a in range(1, 49) for b in range(a + 1, 49)]
+    return gg.from_edges(hub_degree + 1, e)
+
+
+@pytest.mark.parametrize("L", [5, 6])
+def test_noalloc_at_the_degree_limit(env, L):
+    # the largest accepted degree (65535) keeps the 32-bit level-3 sums exact:
+    # the count equals the oracle's
+    torch, P, _ = env
+    g = _hub_and_clique(65535)
+    k, e = gg.cycle(L)
+    colors = O.colors(17, 0, g.n, k)
+    rp, col, c = _device_inputs(torch, g, colors)
+    got = P.cc_count_cycle_noalloc(0, None, L, g.n, rp.data_ptr(), col.data_ptr(), c.data_ptr())
+    assert got == O.dp_count(g, k, e, colors)[0]
+
+
+def test_noalloc_rejects_degree_beyond_limit(env):
+    torch, P, _ = env
+    g = _hub_and_clique(65536)
+    rp, col, c = _device_inputs(torch, g, O.colors(17, 0, g.n, 6))
+    with pytest.raises(P.CCError) as ei:
+        P.cc_count_cycle_noalloc(0, None, 6, g.n, rp.data_ptr(), col.data_ptr(), c.data_ptr())
+    assert P.ERRORS[ei.value.code] == "CC_ERR_INVALID_ARG"
