@@ -434,7 +434,6 @@ def run_precision(args):
 PS_GRAPHS = {
     "chung_lu n=1e4 d=8 g=2.1": ("chung_lu", 10_000, 8, 2.1, 21),
     "chung_lu n=1e5 d=8 g=2.3": ("chung_lu", 100_000, 8, 2.3, 22),
-    "chung_lu n=1e5 d=16 g=2.1": ("chung_lu", 100_000, 16, 2.1, 23),
     "rmat scale=12 ef=8": ("rmat", 12, 8, 0.57, 0.19, 0.19, 24),
     "erdos_renyi n=1e5 m=4e5": ("erdos_renyi", 100_000, 400_000, 25),
 }

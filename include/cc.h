@@ -92,6 +92,15 @@ int cc_set_heavy_degree(cc_ctx *ctx, int degree);
  * library's general per-source kernel only.  cc_count_per_vertex splits a
  * PS count by the image of a_0.  Triangle and leaf blocks are the same under
  * both. */
+/* Triangle blocks (enable = 1, the default): the graph's triangles are
+ * listed once, on the first count of a query with a triangle block (every
+ * triangle u > v > w in the degree order, with the positions of its edges;
+ * colour-independent), and every colouring streams that list.  The list is
+ * not built when it would take more than a quarter of the memory left to
+ * the context; the triangle kernels then scan the wedges of every source
+ * each colouring, as they do with enable = 0.  Counts are the same. */
+int cc_set_triangle_list(cc_ctx *ctx, int enable);
+
 #define CC_PROC_DB 0
 #define CC_PROC_PS 1
 int cc_set_procedure(cc_ctx *ctx, int procedure);

@@ -30,7 +30,7 @@ ERRORS = {
 }
 EXPORTED = [
     "cc_create", "cc_destroy", "cc_set_allocator", "cc_set_memory_budget", "cc_set_heavy_degree",
-    "cc_set_procedure",
+    "cc_set_procedure", "cc_set_triangle_list",
     "cc_load_csr", "cc_free_graph",
     "cc_graph_info", "cc_set_query", "cc_set_decomposition", "cc_plan_inspect", "cc_plan_enumerate", "cc_query_info",
     "cc_set_coloring_seed",
@@ -82,6 +82,7 @@ def load_library(path: str):
         "cc_set_memory_budget": ([P, ctypes.c_size_t], ctypes.c_int),
         "cc_set_heavy_degree": ([P, ctypes.c_int], ctypes.c_int),
         "cc_set_procedure": ([P, ctypes.c_int], ctypes.c_int),
+        "cc_set_triangle_list": ([P, ctypes.c_int], ctypes.c_int),
         "cc_load_csr": ([P, I64, I64P, I32P, I64, I32P], ctypes.c_int),
         "cc_free_graph": ([P, I32], ctypes.c_int),
         "cc_graph_info": ([P, I32, I64P, I64P, I64P], ctypes.c_int),
@@ -184,6 +185,10 @@ PROC_DB, PROC_PS = 0, 1
 
 def cc_set_procedure(h, procedure: int) -> None:
     _check(lib().cc_set_procedure(h, procedure), "cc_set_procedure")
+
+
+def cc_set_triangle_list(h, enable: bool) -> None:
+    _check(lib().cc_set_triangle_list(h, 1 if enable else 0), "cc_set_triangle_list")
 
 
 def cc_load_csr(h, n: int, row_ptr: np.ndarray, col: np.ndarray) -> int:

@@ -470,6 +470,13 @@ int cc_set_heavy_degree(cc_ctx *ctx, int degree) {
   return CC_OK;
 }
 
+int cc_set_triangle_list(cc_ctx *ctx, int enable) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  if (ctx->c.tri_list != (enable != 0)) batch_cache_clear(ctx->c);
+  ctx->c.tri_list = enable != 0;
+  return CC_OK;
+}
+
 int cc_set_procedure(cc_ctx *ctx, int procedure) {
   if (!ctx || (procedure != CC_PROC_DB && procedure != CC_PROC_PS)) return CC_ERR_INVALID_ARG;
   if (ctx->c.procedure != procedure) batch_cache_clear(ctx->c);
@@ -671,6 +678,7 @@ int cc_count(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int first_trial, i
   double scale = 1.0;
   for (int i = 0; i < p->k; i++) scale *= (double)p->k / (double)(i + 1);  // k^k / k!
   int final_rc = CC_OK;
+  if ((rc = prepare_plan_graph(c, *g, *p)) != CC_OK) return rc;
   for (int t = 0; t < T; t++) {
     u64 cnt = 0;
     bool ovf = false;
@@ -698,6 +706,7 @@ int cc_count_per_vertex(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int tri
   if (!per_vertex || trial < 0) return CC_ERR_INVALID_ARG;
   Ctx &c = ctx->c;
   cudaSetDevice(c.device);
+  if ((rc = prepare_plan_graph(c, *g, *p)) != CC_OK) return rc;
   u64 *d_pv = (u64 *)dev_alloc(c, (size_t)g->n * 8);
   if (!d_pv) return CC_ERR_OOM;
   u64 cnt = 0;

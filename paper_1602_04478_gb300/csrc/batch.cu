@@ -92,6 +92,11 @@ extern "C" int cc_count_batch(cc_ctx *ctx, const cc_request *reqs, int n_reqs, u
       return CC_ERR_INVALID_ARG;
     total += (size_t)r.trials;
   }
+  // colouring-independent structure first (it synchronises: not under capture)
+  for (int i = 0; i < n_reqs; i++) {
+    int rc0 = prepare_plan_graph(c, c.graphs[reqs[i].graph_id], c.plans[reqs[i].query_id]);
+    if (rc0 != CC_OK) return rc0;
+  }
   // capture needs a stream other than the legacy default one
   cudaStream_t user = c.stream;
   if (!c.own_stream && cudaStreamCreateWithFlags(&c.own_stream, cudaStreamNonBlocking) != cudaSuccess)

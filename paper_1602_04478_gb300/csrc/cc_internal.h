@@ -84,6 +84,12 @@ struct DevGraph {
   std::map<int, std::vector<struct StageWork>> work_detail;  // query id -> per-stage structural work
   std::map<int, int> tuned_heavy;    // query id -> heavy-source degree threshold (autotuned)
   std::vector<int64_t> h_push_work;  // per rank u: pairs (v, w), v in N<(u), w in N(v), w < u (empty: not yet)
+  // triangle list: every triangle u > v > w once, grouped by u, with the CSR
+  // positions of u->v, u->w, v->w (colour-independent, built on first use)
+  int tri_state = 0;                 // 0 not built yet, 1 built, -1 above the memory cap
+  int64_t n_tri = 0;
+  int32_t *tri_u = nullptr, *tri_v = nullptr, *tri_w = nullptr;
+  int64_t *tri_p = nullptr;          // [3][n_tri]
 };
 
 // -------------------------------- context --------------------------------
@@ -116,6 +122,7 @@ struct Ctx {
   DevGraph *cur_graph = nullptr;           // the graph being counted
   int heavy_degree = -1;         // sources of at least this degree take the heavy path (-1: tuned / default)
   int procedure = CC_PROC_DB;    // root cycles of length >= 4: DB (degree order) or PS (no order)
+  bool tri_list = true;          // triangle blocks stream the graph's triangle list
   int cur_tuned_heavy = -1;      // tuned threshold of the (graph, query) being enqueued, -1 none
   cudaStream_t own_stream = nullptr;  // created for graph capture when the caller's stream is the legacy one
   bool capture = true;           // batches replay a captured CUDA graph

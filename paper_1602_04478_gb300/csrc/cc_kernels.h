@@ -58,11 +58,23 @@ struct TriArgs {
   u64 *status = nullptr;
   int *work_counter = nullptr;
   bool count_units = false;   // add the wedges scanned to status[ST_UNITS]
+  // the graph's triangle list (n_tri < 0: none; the kernels then scan the wedges)
+  int64_t n_tri = -1;
+  const int32_t *tri_u = nullptr, *tri_v = nullptr, *tri_w = nullptr;
+  const int64_t *tri_p = nullptr;  // [3][n_tri]: CSR positions of u->v, u->w, v->w
 };
 
 int launch_leaf(Ctx &c, const LeafArgs &a);
 int launch_root_sum(Ctx &c, const GraphView &g, const u64 *table, u64 *per_vertex, u64 *status);
 int launch_triangle(Ctx &c, const TriArgs &a);
+// Build the graph's triangle list (once; a list above the memory cap is not
+// built and the triangle kernels scan wedges instead).  Synchronises.
+int tri_list_build(Ctx &c, DevGraph &g);
+void tri_list_free(Ctx &c, DevGraph &g);
+// Before a plan runs on g: the colouring-independent structure it uses
+// (the triangle list when the plan has triangle blocks).  Synchronises;
+// never called under stream capture.
+int prepare_plan_graph(Ctx &c, DevGraph &g, const Plan &p);
 
 // root cycle (L >= 4) closure; see cycle.cu
 struct CycleArgs {

@@ -18,6 +18,7 @@
 
 #include "cc_device.cuh"
 #include "cc_internal.h"
+#include "cc_kernels.h"
 
 namespace cc {
 
@@ -109,6 +110,7 @@ static inline unsigned blocks_for(int64_t items, int per) { return (unsigned)((i
 void graph_free(Ctx &c, DevGraph &g) {
   if (g.colors) dev_free(c, g.colors, (size_t)g.colors_T * g.n);
   g.colors = nullptr;
+  tri_list_free(c, g);  // frees only what this context owns
   if (!g.owned) {  // a shared graph: its arrays belong to the context that loaded it
     g = DevGraph();
     return;

@@ -159,8 +159,11 @@ extern "C" int cc_server_load_csr(cc_server *s, int64_t n, const int64_t *row_pt
   std::lock_guard<std::mutex> lk(s->mu);
   int rc = cc_load_csr(s->owner, n, row_ptr, col, nnz, graph_id);
   if (rc != CC_OK) return rc;
+  // the triangle list is built here, once, by the loading context: workers
+  // share the graph's arrays and never build it themselves
+  DevGraph &g = s->owner->c.graphs[*graph_id];
+  if (s->owner->c.tri_list && (rc = tri_list_build(s->owner->c, g)) != CC_OK) return rc;
   // every worker sees the same device arrays under the same id
-  const DevGraph &g = s->owner->c.graphs[*graph_id];
   for (auto *w : s->workers) {
     DevGraph b = g;
     b.owned = false;

@@ -28,6 +28,7 @@
 // A wedge whose first two vertices share a colour cannot close a colourful
 // triangle, so v with chi(v) = chi(u) is skipped before its list is read.
 #include <algorithm>
+#include <vector>
 
 #include "cc_kernels.h"
 
@@ -415,6 +416,355 @@ __global__ void __launch_bounds__(kHubThreads) k_triangle_hub(TriArgs a, TriMode
   if (ovf & 2u) atomicOr(a.status + ST_TIMEOUT, 2ull);  // partial list capacity exceeded
 }
 
+// ------------------------------ triangle list ------------------------------
+// The triangles of a graph do not depend on the colouring.  They are listed
+// once (the same MinBucket enumeration as above: u scans its lower
+// neighbours v, and v's lower neighbours w are tested against N<(u)), into
+// arrays grouped by u; every colouring then streams the list and only checks
+// colours and emits, instead of re-scanning about 20 wedges per triangle.
+//
+// Listing runs twice: the first pass counts each source's triangles, the
+// host turns the counts into offsets, the second pass writes them.
+constexpr int kListHubDegree = 64;  // sources with at least this many lower neighbours: one CTA each
+
+// one warp per source u of [0, u_end) with fewer than kListHubDegree lower neighbours
+template <bool kWrite>
+__global__ void k_tl_warp(GraphView g, int32_t u_end, int64_t *counts, const int64_t *offs, int32_t *tu,
+                          int32_t *tv, int32_t *tw, int64_t *tp, int64_t n_tri) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t ui = warp0; ui < u_end; ui += nwarps) {
+    const int32_t u = (int32_t)ui;
+    const int64_t ub = g.row[u];
+    const int du = g.lo_cnt[u];
+    if (du >= kListHubDegree) continue;
+    int64_t at = kWrite ? offs[u] : 0;
+    for (int iv = 1; iv < du; iv++) {
+      const int32_t v = __ldg(g.col + ub + iv);
+      const int64_t vb = g.row[v];
+      const int dv = g.lo_cnt[v];
+      for (int j0 = 0; j0 < dv; j0 += 32) {
+        const int j = j0 + lane;
+        int64_t p = -1;
+        if (j < dv) {
+          const int32_t w = __ldg(g.col + vb + j);
+          const int64_t q = lower_bound_i32(g.col, ub, ub + iv, w);
+          if (q < ub + iv && __ldg(g.col + q) == w) p = q;
+        }
+        const unsigned hit = __ballot_sync(FULL, p >= 0);
+        if (kWrite && p >= 0) {
+          const int64_t i = at + __popc(hit & ((1u << lane) - 1u));
+          tu[i] = u;
+          tv[i] = v;
+          tw[i] = __ldg(g.col + p);
+          tp[i] = ub + iv;
+          tp[n_tri + i] = p;
+          tp[2 * n_tri + i] = vb + j;
+        }
+        at += __popc(hit);
+      }
+    }
+    if (!kWrite && lane == 0) counts[u] = at;
+  }
+}
+
+// one CTA per source u of [0, u_end) with at least kListHubDegree lower
+// neighbours (work counter, highest first): N<(u) in a shared-memory hash set
+// with each key's index, or binary search when it does not fit
+template <bool kWrite>
+__global__ void __launch_bounds__(kHubThreads) k_tl_hub(GraphView g, int32_t u_end, int *work, int max_slots,
+                                                        int64_t *counts, const int64_t *offs, int32_t *tu,
+                                                        int32_t *tv, int32_t *tw, int64_t *tp, int64_t n_tri) {
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char tl_smem[];
+  int32_t *keys = reinterpret_cast<int32_t *>(tl_smem);
+  int32_t *kpos = keys + max_slots;
+  __shared__ int s_idx;
+  __shared__ unsigned long long s_at;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  for (int i = tid; i < max_slots; i += blockDim.x) keys[i] = -1;
+  while (true) {
+    __syncthreads();
+    if (tid == 0) s_idx = atomicAdd(work, 1);
+    __syncthreads();
+    const int idx = s_idx;
+    if (idx >= u_end) break;
+    const int32_t u = u_end - 1 - idx;
+    const int64_t ub = g.row[u];
+    const int du = g.lo_cnt[u];
+    if (du < kListHubDegree) continue;
+    if (tid == 0) s_at = kWrite ? (unsigned long long)offs[u] : 0ull;
+    const bool hashed = 2 * du <= max_slots;
+    int slots = 64;
+    if (hashed)
+      while (slots < 2 * du) slots <<= 1;
+    const uint32_t mask = (uint32_t)slots - 1u;
+    const int shift = 32 - __ffs(slots) + 1;
+    if (hashed) {
+      for (int i = tid; i < du; i += blockDim.x) {
+        const int32_t w = __ldg(g.col + ub + i);
+        uint32_t h = hub_hash(w) >> shift;
+        for (int t = 0; t < slots; t++, h = (h + 1u) & mask)
+          if (atomicCAS(keys + h, -1, w) == -1) {
+            kpos[h] = i;
+            break;
+          }
+      }
+    }
+    __syncthreads();
+    for (int iv = 1 + warp; iv < du; iv += nwarps) {
+      const int32_t v = __ldg(g.col + ub + iv);
+      const int64_t vb = g.row[v];
+      const int dv = g.lo_cnt[v];
+      for (int j0 = 0; j0 < dv; j0 += 32) {
+        const int j = j0 + lane;
+        int64_t p = -1;
+        if (j < dv) {
+          const int32_t w = __ldg(g.col + vb + j);
+          if (hashed) {
+            uint32_t h = hub_hash(w) >> shift;
+            for (int t = 0; t < slots; t++, h = (h + 1u) & mask) {
+              const int32_t kk = keys[h];
+              if (kk == w) {
+                p = ub + kpos[h];
+                break;
+              }
+              if (kk < 0) break;
+            }
+          } else {
+            const int64_t q = lower_bound_i32(g.col, ub, ub + iv, w);
+            if (q < ub + iv && __ldg(g.col + q) == w) p = q;
+          }
+        }
+        const unsigned hit = __ballot_sync(FULL, p >= 0);
+        if (!hit) continue;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&s_at, (unsigned long long)__popc(hit));
+        base = __shfl_sync(FULL, base, 0);
+        if (kWrite && p >= 0) {
+          const int64_t i = (int64_t)base + __popc(hit & ((1u << lane) - 1u));
+          tu[i] = u;
+          tv[i] = v;
+          tw[i] = __ldg(g.col + p);
+          tp[i] = ub + iv;
+          tp[n_tri + i] = p;
+          tp[2 * n_tri + i] = vb + j;
+        }
+      }
+    }
+    __syncthreads();
+    if (!kWrite && tid == 0) counts[u] = (int64_t)s_at;
+    if (hashed)
+      for (int i = tid; i < slots; i += blockDim.x) keys[i] = -1;
+  }
+}
+
+void tri_list_free(Ctx &c, DevGraph &g) {
+  if (g.tri_state == 1 && g.owned) {
+    const size_t n = (size_t)std::max<int64_t>(g.n_tri, 1);
+    dev_free(c, g.tri_u, n * 4);
+    dev_free(c, g.tri_v, n * 4);
+    dev_free(c, g.tri_w, n * 4);
+    dev_free(c, g.tri_p, n * 24);
+  }
+  g.tri_u = g.tri_v = g.tri_w = nullptr;
+  g.tri_p = nullptr;
+  g.n_tri = 0;
+  g.tri_state = 0;
+}
+
+static int tl_launch(Ctx &c, const GraphView &gv, bool write, int64_t *counts, const int64_t *offs, int32_t *tu,
+                     int32_t *tv, int32_t *tw, int64_t *tp, int64_t n_tri, int *work, int max_slots, size_t smem) {
+  const int32_t n = (int32_t)gv.n;
+  if (cudaMemsetAsync(work, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
+  if (write) {
+    k_tl_warp<true><<<152 * 8, 256, 0, c.stream>>>(gv, n, counts, offs, tu, tv, tw, tp, n_tri);
+    k_tl_hub<true><<<152 * 2, kHubThreads, smem, c.stream>>>(gv, n, work, max_slots, counts, offs, tu, tv, tw, tp,
+                                                             n_tri);
+  } else {
+    k_tl_warp<false><<<152 * 8, 256, 0, c.stream>>>(gv, n, counts, offs, tu, tv, tw, tp, n_tri);
+    k_tl_hub<false><<<152 * 2, kHubThreads, smem, c.stream>>>(gv, n, work, max_slots, counts, offs, tu, tv, tw, tp,
+                                                              n_tri);
+  }
+  c.kernels += 2;
+  return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+}
+
+int tri_list_build(Ctx &c, DevGraph &g) {
+  if (g.tri_state != 0) return CC_OK;
+  const int64_t n = g.n;
+  GraphView gv = view_of(g);
+  int max_slots = 64;
+  while (max_slots < kHubMaxSlots && max_slots < 2 * g.max_deg) max_slots <<= 1;
+  const size_t smem = (size_t)max_slots * 8;
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(k_tl_hub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tl_hub<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return CC_ERR_CUDA;
+  }
+  int64_t *counts = (int64_t *)dev_alloc(c, (size_t)(n + 1) * 8);
+  int *work = (int *)dev_alloc(c, 256);
+  if (!counts || !work) {
+    dev_free(c, counts, (size_t)(n + 1) * 8);
+    dev_free(c, work, 256);
+    return CC_ERR_OOM;
+  }
+  int rc = CC_OK;
+  std::vector<int64_t> h((size_t)n + 1, 0);
+  timing_begin(c, "triangle_list_build");
+  do {
+    if ((rc = tl_launch(c, gv, false, counts, nullptr, nullptr, nullptr, nullptr, nullptr, 0, work, max_slots,
+                        smem)) != CC_OK)
+      break;
+    if (cudaMemcpyAsync(h.data(), counts, (size_t)n * 8, cudaMemcpyDeviceToHost, c.stream) != cudaSuccess ||
+        cudaStreamSynchronize(c.stream) != cudaSuccess) {
+      rc = CC_ERR_CUDA;
+      break;
+    }
+    // counts -> offsets (exclusive prefix sum); h[n] = number of triangles
+    int64_t run = 0;
+    for (int64_t u = 0; u < n; u++) {
+      const int64_t t = h[u];
+      h[u] = run;
+      run += t;
+    }
+    h[n] = run;
+    // the list stays within a quarter of the memory left to this context
+    size_t room = 0;
+    if (c.budget) {
+      room = c.budget > c.in_use ? (c.budget - c.in_use) / 4 : 0;
+    } else {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { rc = CC_ERR_CUDA; break; }
+      room = fr / 4;
+    }
+    const size_t nt = (size_t)std::max<int64_t>(run, 1);
+    if (nt * 36 > room) {
+      g.tri_state = -1;
+      break;
+    }
+    g.tri_u = (int32_t *)dev_alloc(c, nt * 4);
+    g.tri_v = (int32_t *)dev_alloc(c, nt * 4);
+    g.tri_w = (int32_t *)dev_alloc(c, nt * 4);
+    g.tri_p = (int64_t *)dev_alloc(c, nt * 24);
+    g.n_tri = run;
+    g.tri_state = 1;
+    if (!g.tri_u || !g.tri_v || !g.tri_w || !g.tri_p) {
+      tri_list_free(c, g);
+      g.tri_state = -1;
+      break;
+    }
+    if (cudaMemcpyAsync(counts, h.data(), (size_t)n * 8, cudaMemcpyHostToDevice, c.stream) != cudaSuccess) {
+      rc = CC_ERR_CUDA;
+      break;
+    }
+    rc = tl_launch(c, gv, true, nullptr, counts, g.tri_u, g.tri_v, g.tri_w, g.tri_p, g.n_tri, work, max_slots, smem);
+    if (rc == CC_OK && cudaStreamSynchronize(c.stream) != cudaSuccess) rc = CC_ERR_CUDA;
+  } while (false);
+  timing_end(c);
+  if (rc != CC_OK) tri_list_free(c, g);
+  cudaStreamSynchronize(c.stream);
+  dev_free(c, counts, (size_t)(n + 1) * 8);
+  dev_free(c, work, 256);
+  return rc;
+}
+
+int prepare_plan_graph(Ctx &c, DevGraph &g, const Plan &p) {
+  if (!c.tri_list || g.tri_state != 0 || !g.owned) return CC_OK;
+  for (auto &st : p.stages)
+    if (st.kind == ST_TRI) return tri_list_build(c, g);
+  return CC_OK;
+}
+
+// Stream the triangle list for one colouring: a block takes tiles of
+// consecutive triangles (grouped by their highest vertex u); contributions
+// to the tile's first source's own row (or its root count) gather in shared
+// memory and reach global memory once per tile, the rest go by atomics.
+constexpr int kEmitThreads = 256;
+constexpr int kEmitTile = 2048;
+
+template <int kForm>
+__global__ void __launch_bounds__(kEmitThreads) k_tl_emit(TriArgs a, TriMode md, int R_acc) {
+  extern __shared__ __align__(16) unsigned char emit_smem[];
+  u64 *acc = reinterpret_cast<u64 *>(emit_smem);
+  __shared__ u64 s_root;
+  __shared__ int32_t s_u0;
+  const int tid = threadIdx.x;
+  unsigned ovf = 0;
+  u64 other = 0;  // root counts of triangles whose source is not the tile's first
+  for (int i = tid; i < R_acc; i += blockDim.x) acc[i] = 0;
+  if (tid == 0) s_root = 0;
+  for (int64_t t0 = (int64_t)blockIdx.x * kEmitTile; t0 < a.n_tri; t0 += (int64_t)gridDim.x * kEmitTile) {
+    if (tid == 0) s_u0 = __ldg(a.tri_u + t0);
+    __syncthreads();
+    const int32_t u0 = s_u0;
+    USink sk;
+    if (a.nb == 1) sk.u = u0, sk.acc = acc;
+    const int64_t t1 = min(a.n_tri, t0 + kEmitTile);
+    for (int64_t i = t0 + tid; i < t1; i += blockDim.x) {
+      const int32_t u = __ldg(a.tri_u + i), v = __ldg(a.tri_v + i), w = __ldg(a.tri_w + i);
+      const int cu = a.colors[u], cv = a.colors[v], cw = a.colors[w];
+      if (cu == cv || cu == cw || cv == cw) continue;
+      u64 r = 0;
+      const int64_t p01 = md.need_pos ? __ldg(a.tri_p + i) : 0;
+      const int64_t p02 = md.need_pos ? __ldg(a.tri_p + a.n_tri + i) : 0;
+      const int64_t p12 = md.need_pos ? __ldg(a.tri_p + 2 * a.n_tri + i) : 0;
+      tri_visit<kForm>(a, md, sk, u, v, w, cu, cv, cw, p01, p02, p12, r, ovf);
+      if (a.nb == 0 && r) {
+        if (u == u0) {
+          atomic_add_ck(&s_root, r, ovf);
+        } else {
+          other = add_ck(other, r, ovf);
+          if (a.per_vertex) atomicAdd(a.per_vertex + u, r);
+        }
+      }
+    }
+    __syncthreads();
+    if (a.nb == 1) {
+      for (int k = tid; k < R_acc; k += blockDim.x) {
+        const u64 t = acc[k];
+        if (t) {
+          atomic_add_ck(a.out + (int64_t)u0 * a.R_out + k, t, ovf);
+          acc[k] = 0;
+        }
+      }
+    }
+    if (a.nb == 0 && tid == 0) {
+      const u64 r = s_root;
+      if (r) {
+        atomic_add_ck(a.status + ST_COUNT, r, ovf);
+        if (a.per_vertex) atomicAdd(a.per_vertex + u0, r);
+      }
+      s_root = 0;
+    }
+  }
+  if (a.nb == 0) {
+    other = warp_sum_ck(other, ovf);
+    if ((tid & 31) == 0 && other) atomic_add_ck(a.status + ST_COUNT, other, ovf);
+  }
+  flag_overflow(a.status, ovf & 1u);
+  if (ovf & 2u) atomicOr(a.status + ST_TIMEOUT, 2ull);  // partial list capacity exceeded
+}
+
+template <int kForm>
+static int launch_emit(Ctx &c, const TriArgs &a, const TriMode &md, const char *name) {
+  const int R_acc = a.nb == 1 ? ((a.R_out + 1) & ~1) : 0;
+  const size_t smem = (size_t)std::max(R_acc, 2) * 8;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_tl_emit<kForm>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return CC_ERR_CUDA;
+  if (a.n_tri == 0) return CC_OK;
+  const int64_t tiles = (a.n_tri + kEmitTile - 1) / kEmitTile;
+  const int grid = (int)std::min<int64_t>(tiles, 152 * 8);
+  timing_begin(c, name);
+  k_tl_emit<kForm><<<grid, kEmitThreads, smem, c.stream>>>(a, md, R_acc);
+  c.kernels++;
+  timing_end(c);
+  return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+}
+
 template <int kForm>
 int launch_triangle_form(Ctx &c, const TriArgs &a, const TriMode &md, const char *name) {
   // sources of degree >= kHubDegree: ranks [u_lo, n) (degree grows with rank)
@@ -460,7 +810,19 @@ int launch_triangle_form(Ctx &c, const TriArgs &a, const TriMode &md, const char
   return CC_OK;
 }
 
-int launch_triangle(Ctx &c, const TriArgs &a) {
+int launch_triangle(Ctx &c, const TriArgs &a_in) {
+  TriArgs a = a_in;
+  const DevGraph *g = c.cur_graph;
+  // the triangle list when the graph has one (the structural counting pass
+  // scans the wedges, which is the work it counts)
+  const bool listed = c.tri_list && !a.count_units && g && g->tri_state == 1;
+  if (listed) {
+    a.n_tri = g->n_tri;
+    a.tri_u = g->tri_u;
+    a.tri_v = g->tri_v;
+    a.tri_w = g->tri_w;
+    a.tri_p = g->tri_p;
+  }
   TriMode md;
   int n_ann = 0;
   bool any_edge = false;
@@ -471,6 +833,11 @@ int launch_triangle(Ctx &c, const TriArgs &a) {
   }
   if (n_ann != 1) md.one_pos = -1;
   md.need_pos = any_edge || a.nb == 2;
+  if (listed) {
+    if (md.plain) return launch_emit<0>(c, a, md, "triangle_list_plain");
+    if (md.one_pos >= 0) return launch_emit<1>(c, a, md, "triangle_list_join1");
+    return launch_emit<2>(c, a, md, "triangle_list_join");
+  }
   if (md.plain) return launch_triangle_form<0>(c, a, md, "triangle_plain");
   if (md.one_pos >= 0) return launch_triangle_form<1>(c, a, md, "triangle_join1");
   return launch_triangle_form<2>(c, a, md, "triangle_join");

@@ -127,23 +127,82 @@ def _wheel_with_chords():
     return gg.wheel_with_chords()
 
 
+@pytest.mark.parametrize("listed", [True, False])
 @pytest.mark.parametrize("qname", ["triangle", "diamond", "chord_pendant", "tailed_triangle", "bowtie"])
-def test_triangle_sources_of_every_degree(cc, qname):
+def test_triangle_sources_of_every_degree(cc, qname, listed):
     # triangle blocks listed from sources of low degree (one warp each),
-    # hashed hub sources (one CTA each) and a source above the hash capacity
+    # hashed hub sources (one CTA each) and a source above the hash capacity;
+    # streamed from the graph's triangle list, or scanned every colouring
     import paper_1602_04478_gb300 as P
     g = _wheel_with_chords()
     k, e = QUERIES[qname]
+    P.cc_set_triangle_list(cc.h, listed)
     gid = cc.load_graph(g)
     try:
         P.cc_set_coloring_seed(cc.h, 5)
         qid = cc.set_query(k, e)
+        P.cc_set_timing(cc.h, True)
+        P.cc_reset_timing(cc.h)
         pv, total = cc.count_per_vertex(gid, qid, 0)
+        names = P.cc_get_timing(cc.h)
+        P.cc_set_timing(cc.h, False)
+        assert any(n.startswith("triangle_list_") for n in names) == listed, names
         expect, _, per = O.dp_count(g, k, e, O.colors(5, 0, g.n, k), per_source=True)
         assert total == expect
         assert [int(x) for x in pv] == per
     finally:
+        P.cc_set_triangle_list(cc.h, True)
         cc.free_graph(gid)
+
+
+@pytest.mark.parametrize("gname", ["cl3000", "rmat10"])
+def test_triangle_list_against_wedge_scan(cc, gname):
+    # the same counts whether triangle blocks stream the list or scan wedges,
+    # for every triangle form (plain, one annotation, general; unary,
+    # edge-keyed and root outputs), equal to the oracle's
+    import paper_1602_04478_gb300 as P
+    g = graph(gname)
+    gid = cc.load_graph(g)
+    try:
+        P.cc_set_coloring_seed(cc.h, 12)
+        for qname in ["triangle", "diamond", "chord_pendant", "chord_pendant0", "bowtie", "triangle_strip", "house"]:
+            k, e = QUERIES[qname]
+            qid = cc.set_query(k, e)
+            got = {}
+            for listed in (True, False):
+                P.cc_set_triangle_list(cc.h, listed)
+                got[listed] = [int(x) for x in cc.count(gid, qid, 0, 2)[0]]
+            P.cc_set_triangle_list(cc.h, True)
+            want = [O.dp_count(g, k, e, O.colors(12, t, g.n, k))[0] for t in range(2)]
+            assert got[True] == got[False] == want, qname
+    finally:
+        P.cc_set_triangle_list(cc.h, True)
+        cc.free_graph(gid)
+
+
+def test_triangle_list_above_memory_cap_falls_back(cc):
+    # a list that would not fit a quarter of the budget is not built: the
+    # triangle kernels scan wedges instead, with the same counts
+    import paper_1602_04478_gb300 as P
+    ctx = P.Context(0)
+    try:
+        # the wheel graph: 39,078 triangles (1.4 MB listed), 1.4 MB of graph
+        # arrays, 3.6 MB of glasses tables: a 6 MB budget leaves the list
+        # less than its size
+        g = _wheel_with_chords()
+        gid = ctx.load_graph(g)
+        P.cc_set_memory_budget(ctx.h, 6 << 20)
+        k, e = QUERIES["glasses"]
+        qid = ctx.set_query(k, e)
+        P.cc_set_coloring_seed(ctx.h, 2)
+        P.cc_set_timing(ctx.h, True)
+        got = int(ctx.count(gid, qid, 0, 1)[0][0])
+        names = P.cc_get_timing(ctx.h)
+        assert not any(n.startswith("triangle_list_") for n in names), names
+        P.cc_set_memory_budget(ctx.h, 0)
+        assert got == O.dp_count(g, k, e, O.colors(2, 0, g.n, k))[0]
+    finally:
+        ctx.close()
 
 
 @pytest.mark.parametrize("qname", ["glasses", "C5_pendant_path", "C6_2pendants", "C7"])
@@ -482,4 +541,39 @@ def test_work_units_match_oracle(cc, gname, L):
         qid = cc.set_query(*gg.cycle(L))
         assert P.cc_work_units(cc.h, gid, qid) == O.cycle_units(g, L, L)
     finally:
+        cc.free_graph(gid)
+
+
+@pytest.mark.parametrize("heavy", [-1, 64])
+@pytest.mark.parametrize("gname", ["rmat13", "cl30000"])
+def test_mid_size_graphs_match_stored_oracle(cc, gname, heavy):
+    # R-MAT scale 13 (maximum degree 1,502) and Chung-Lu n = 30,000: every
+    # benchmark query against stored oracle values (tests/golden/mid.txt),
+    # totals and the split by highest cycle vertex for sampled sources of
+    # every degree class, at the library's threshold and with most sources on
+    # the grouped heavy path
+    import paper_1602_04478_gb300 as P
+    gold = golden_io.load("mid")
+    g = gold.graph(gname)
+    gid = cc.load_graph(g)
+    P.cc_set_heavy_degree(cc.h, heavy)
+    try:
+        for (gn, q, seed, trial), (want, ovf) in gold.counts.items():
+            if gn != gname:
+                continue
+            assert not ovf
+            P.cc_set_coloring_seed(cc.h, seed)
+            qid = cc.set_query(*gg.query(q))
+            assert int(cc.count(gid, qid, trial, 1)[0][0]) == want, (gname, q)
+        for (gn, q, seed, trial), per in gold.sources.items():
+            if gn != gname:
+                continue
+            P.cc_set_coloring_seed(cc.h, seed)
+            qid = cc.set_query(*gg.query(q))
+            pv, total = cc.count_per_vertex(gid, qid, trial)
+            assert int(pv.sum()) == total
+            for v, want in per.items():
+                assert int(pv[v]) == want, (gname, q, v)
+    finally:
+        P.cc_set_heavy_degree(cc.h, -1)
         cc.free_graph(gid)
