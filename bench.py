@@ -55,7 +55,7 @@ BATCH_QUERIES = ["C5", "chord_pendant", "glasses"]
 TRAFFIC_BYTES = {"cycle_closure": None, "leaf_join": None, "triangle": None}
 FLUSH_BYTES = 256 << 20
 # CPU baseline: whole colourings on a smaller graph of the benchmark's shape
-CPU_GRAPH = {"graph": "chung_lu", "n": 20_000, "mean_deg": 16, "gamma": 2.1, "seed": 2}
+CPU_GRAPH = {"graph": "chung_lu", "n": 2_000, "mean_deg": 16, "gamma": 2.1, "seed": 2}
 
 
 def rank_trials(rank: int, count: int, offset: int = 0):
@@ -201,6 +201,15 @@ def _cpu_step(trial):
     return secs
 
 
+def _cpu_warm(_):
+    """Worker start-up outside the timed region: imports and the oracle library."""
+    import graphgen as gg
+    import oracle as O
+    O.colors(1, 0, 1, 2)
+    gg.chung_lu(CPU_GRAPH["n"], CPU_GRAPH["mean_deg"], CPU_GRAPH["gamma"], CPU_GRAPH["seed"])
+    return 0
+
+
 def oracle_baseline(rounds: int = 1):
     """The oracle as it stands on the host: one step alone (1 core), then one
     step per core in parallel (spawned worker processes, distinct colourings),
@@ -215,7 +224,7 @@ def oracle_baseline(rounds: int = 1):
     cores = os.cpu_count() or 1
     one = _cpu_step(0)
     with ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
-        list(ex.map(_cpu_step, range(cores)))  # warm-up: imports, oracle build
+        list(ex.map(_cpu_warm, range(cores)))  # warm-up: imports, oracle library
         t0 = time.perf_counter()
         list(ex.map(_cpu_step, range(100, 100 + rounds * cores)))
         wall = time.perf_counter() - t0
@@ -227,7 +236,7 @@ def oracle_baseline(rounds: int = 1):
             "cpu_model": cpu_model(), "nproc": cores,
             "sample": (f"whole colourings (C6 + glasses per step, {steps} steps, one per core in spawned "
                        f"processes, {wall:.1f} s wall) on chung_lu n={w['n']} mean_deg={w['mean_deg']} "
-                       f"gamma={w['gamma']} seed={w['seed']}, the benchmark graph's shape at 1/50 of its size; "
+                       f"gamma={w['gamma']} seed={w['seed']}, the benchmark graph's shape at 1/500 of its size; "
                        f"{units_step:.4g} updates per step")}
 
 
@@ -581,20 +590,33 @@ def run_plan_eval(args):
 
 
 def run_profile_case(args):
-    """One colouring of one query on the benchmark graph, nothing else: the
-    command a profiler wraps to capture a few launches of one kernel."""
+    """Count QUERY (comma-separated list) for `--profile-reps` colourings on a
+    Chung-Lu graph of the benchmark's shape (n = --profile-n, mean degree
+    --profile-mean; the benchmark graph by default) after one untimed
+    colouring that builds the per-graph structure: the command a profiler
+    wraps to capture a few launches of one kernel.  Prints the algorithmic
+    bytes of each stage of each query (cc_work_detail) beside the counts."""
     import graphgen as gg
     import paper_1602_04478_gb300 as P
 
-    g = make_graph()
-    ctx = P.Context(0)
+    w = WORKLOAD
+    n = args.profile_n or w["n"]
+    mean = args.profile_mean or w["mean_deg"]
+    g = gg.chung_lu(n, mean, w["gamma"], w["seed"])
+    ctx = P.Context(0, budget_bytes=int(args.profile_budget * (1 << 30)))
     gid = ctx.load_graph(g)
     P.cc_set_coloring_seed(ctx.h, COLOR_SEED)
-    P.cc_set_heavy_degree(ctx.h, args.heavy_degree if args.heavy_degree >= 0 else 256)
-    q = ctx.set_query(*gg.query(args.profile_case))
-    col, _, _ = ctx.count(gid, q, 0, 1)
-    print(json.dumps({"profile_case": args.profile_case, "colorful": int(col[0]),
-                      "kernel_launches": P.cc_kernel_launches(ctx.h)}))
+    P.cc_set_heavy_degree(ctx.h, args.heavy_degree if args.heavy_degree >= 0 else 384)
+    out = {"profile_case": args.profile_case, "n": n, "mean_deg": mean, "heavy_degree": args.heavy_degree,
+           "budget_gib": args.profile_budget, "queries": {}}
+    for name in args.profile_case.split(","):
+        q = ctx.set_query(*gg.query(name))
+        detail = P.cc_work_detail(ctx.h, gid, q)
+        ctx.count(gid, q, 100, 1, allow_overflow=True)  # per-graph structure, outside the captured launches
+        cols = [int(ctx.count(gid, q, t, 1, allow_overflow=True)[0][0]) for t in range(args.profile_reps)]
+        out["queries"][name] = {"colorful": cols, "stages": detail}
+    out["kernel_launches"] = P.cc_kernel_launches(ctx.h)
+    print(json.dumps(out))
     ctx.close()
 
 
@@ -617,7 +639,12 @@ def main():
     ap.add_argument("--heavy-degree", type=int, default=-1,
                     help="heavy/light source degree threshold (default: autotuned)")
     ap.add_argument("--profile-case", default=None, metavar="QUERY",
-                    help="count QUERY once on the benchmark graph (one colouring, no timing) for profiler captures")
+                    help="count QUERY (comma-separated) on a benchmark-shaped graph for profiler captures")
+    ap.add_argument("--profile-n", type=int, default=0, help="graph size of --profile-case (0: the benchmark's)")
+    ap.add_argument("--profile-mean", type=float, default=0, help="mean degree of --profile-case (0: 16)")
+    ap.add_argument("--profile-reps", type=int, default=1, help="colourings counted by --profile-case")
+    ap.add_argument("--profile-budget", type=float, default=0,
+                    help="device memory budget of --profile-case in GiB (0: none); caps the per-CTA push's slots")
     ap.add_argument("--rmat-pendants", action="store_true",
                     help="R-MAT graph with the 8-node 6-cycle-with-two-pendants query instead")
     ap.add_argument("--rmat-scale", type=int, default=22)
