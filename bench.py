@@ -568,15 +568,18 @@ def run_plan_eval(args):
                     best = ms if best is None else min(best, ms)
                     counts.add(int(col[0]))
                 times.append(best)
-            h = [i for i, t in enumerate(trees) if t["default"]][0]
-            # the paper's order of factors over the supported trees
+            # the paper's heuristic (its factors alone) and the library's pick
+            h = [i for i, t in enumerate(trees) if t["paper"]][0]
+            lib_pick = [i for i, t in enumerate(trees) if t["default"]][0]
             key = [(t["longest"], t["boundary"], t["annotations"]) for t in trees]
             ties = [i for i in range(len(trees)) if key[i] == key[h]]
             opt = min(range(len(trees)), key=lambda i: times[i])
             row = {"graph": gname, "query": q, "trees": len(trees), "ms": times, "heuristic": h, "optimal": opt,
                    "heuristic_is_optimal": h == opt, "heuristic_over_optimal": times[h] / times[opt],
+                   "library_pick": lib_pick, "library_is_optimal": lib_pick == opt,
+                   "library_over_optimal": times[lib_pick] / times[opt],
                    "trees_tied_with_heuristic": len(ties), "counts_equal": len(counts) == 1,
-                   "factors": key}
+                   "factors": key, "join_cost": [t["cost"] for t in trees]}
             rows.append(row)
             print(json.dumps({"partial": True, **row}), flush=True)
         ctx.free_graph(gid)
@@ -584,6 +587,9 @@ def run_plan_eval(args):
                       "heuristic_optimal_share": sum(r["heuristic_is_optimal"] for r in rows) / max(1, len(rows)),
                       "within_15pct_share": sum(r["heuristic_over_optimal"] <= 1.15 for r in rows) / max(1, len(rows)),
                       "max_heuristic_over_optimal": max((r["heuristic_over_optimal"] for r in rows), default=None),
+                      "library_optimal_share": sum(r["library_is_optimal"] for r in rows) / max(1, len(rows)),
+                      "library_within_15pct_share": sum(r["library_over_optimal"] <= 1.15 for r in rows) / max(1, len(rows)),
+                      "max_library_over_optimal": max((r["library_over_optimal"] for r in rows), default=None),
                       "all_counts_equal": all(r["counts_equal"] for r in rows), "per_pair": rows}), flush=True)
     ctx.close()
     return 0

@@ -154,12 +154,19 @@ int cc_plan_inspect(int k, int n_edges, const int32_t *edges, const int32_t *blo
  * per distinct tree -- sequence length m, supported (1 when the library has
  * kernels for every block), the paper's ranking factors (longest cycle
  * block, number of boundary nodes, number of annotations, each summed over
- * the blocks), 1 when it is the tree cc_set_query picks, then the m-word
- * contraction sequence in cc_set_decomposition's block_seq format -- into
- * out[cap].  *n_plans (nullable) receives the number of trees.  Returns the
- * number of int32 words (more than cap means truncated) or a CC_ERR_ code.
- * cc_set_query picks, among the supported trees, the least by the paper's
- * factors in order (Section 5.3's heuristic). */
+ * the blocks), 1 when it is the tree cc_set_query picks, 1 when it is the
+ * tree the paper's factors alone pick, the library's join cost (rounded),
+ * then the m-word contraction sequence in cc_set_decomposition's block_seq
+ * format -- into out[cap].  *n_plans (nullable) receives the number of
+ * trees.  Returns the number of int32 words (more than cap means truncated)
+ * or a CC_ERR_ code.
+ * cc_set_query picks, among the supported trees, the least by: longest
+ * cycle block (the paper's first factor), then the join cost -- per data
+ * triangle (taken as three per edge) six node assignments times the product
+ * of the annotating blocks' row lengths, four times that for a triangle
+ * with two or more annotations, twice for an edge-keyed output; per data
+ * edge of a leaf block the product of its annotating row lengths -- then
+ * the paper's remaining factors (boundary nodes, annotations). */
 int cc_plan_enumerate(int k, int n_edges, const int32_t *edges, int32_t *out, int cap, int *n_plans);
 
 /* Query facts: k, aut(Q), number of blocks, longest cycle block. */

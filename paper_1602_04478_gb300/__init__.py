@@ -271,7 +271,8 @@ def cc_plan_inspect(k: int, edges, block_seq=None, allow_unsupported: bool = Fal
 def cc_plan_enumerate(k: int, edges):
     """Every decomposition tree of the query (host only): list of dicts with
     the contraction sequence (for cc_set_decomposition), whether the library
-    supports it, the paper's ranking factors and whether cc_set_query picks it."""
+    supports it, the paper's ranking factors, the library's join cost, and
+    whether cc_set_query (default) or the paper's factors alone (paper) pick it."""
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
     out = np.zeros(1 << 16, dtype=np.int32)
     n = ctypes.c_int(0)
@@ -283,9 +284,9 @@ def cc_plan_enumerate(k: int, edges):
     while i < min(w, out.size):
         m = int(out[i])
         plans.append({"supported": bool(out[i + 1]), "longest": int(out[i + 2]), "boundary": int(out[i + 3]),
-                      "annotations": int(out[i + 4]), "default": bool(out[i + 5]),
-                      "seq": [int(x) for x in out[i + 6:i + 6 + m]]})
-        i += 6 + m
+                      "annotations": int(out[i + 4]), "default": bool(out[i + 5]), "paper": bool(out[i + 6]),
+                      "cost": int(out[i + 7]), "seq": [int(x) for x in out[i + 8:i + 8 + m]]})
+        i += 8 + m
     return plans
 
 

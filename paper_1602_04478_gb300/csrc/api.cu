@@ -608,6 +608,8 @@ int cc_plan_enumerate(int k, int n_edges, const int32_t *edges, int32_t *out, in
     put(p.boundary);
     put(p.annotations);
     put(p.is_default);
+    put(p.is_paper);
+    put((int32_t)std::min(p.cost, 2.0e9));
     for (int x : p.seq) put(x);
   }
   if (n_plans) *n_plans = (int)plans.size();

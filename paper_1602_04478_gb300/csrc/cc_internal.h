@@ -43,7 +43,9 @@ struct Plan {
 
 // Builds the default plan (searching decomposition orders) or applies an
 // explicit order.  Returns a CC_ status code.
-int plan_query(int k, const std::vector<std::pair<int, int>> &edges, Plan &out);
+// paper_only: rank trees by the paper's factors alone (Section 5.3), without
+// the library's engine-aware cost factor
+int plan_query(int k, const std::vector<std::pair<int, int>> &edges, Plan &out, bool paper_only = false);
 int plan_explicit(int k, const std::vector<std::pair<int, int>> &edges,
                   const std::vector<int> &block_seq, Plan &out);
 int64_t count_automorphisms(int k, const std::vector<std::pair<int, int>> &edges);
@@ -52,8 +54,9 @@ int64_t count_automorphisms(int k, const std::vector<std::pair<int, int>> &edges
 // block_seq) and the paper's ranking factors (Section 5.3).
 struct PlanChoice {
   std::vector<int> seq;
-  bool supported = false, is_default = false;
+  bool supported = false, is_default = false, is_paper = false;
   int longest = 0, boundary = 0, annotations = 0;
+  double cost = 0;  // the library's engine-aware join cost
 };
 int plan_enumerate(int k, const std::vector<std::pair<int, int>> &edges, std::vector<PlanChoice> &out);
 

@@ -238,19 +238,63 @@ bool try_root(QS &s, std::vector<Stage> &st, bool *ok) {
   return false;
 }
 
+// Ranking of a decomposition tree.  The paper's factors, in its order
+// (Section 5.3): longest cycle block, boundary nodes, annotations.  The
+// library inserts one engine-aware factor after the longest cycle (see
+// join_cost) unless `paper_only`.
 struct Score {
-  int unsupported, longest, boundary, annotations, stages;
+  int unsupported, longest;
+  double cost;
+  int boundary, annotations, stages;
+  bool paper_only;
   bool operator<(const Score &o) const {
     if (unsupported != o.unsupported) return unsupported < o.unsupported;
     if (longest != o.longest) return longest < o.longest;
+    if (!paper_only && cost != o.cost) return cost < o.cost;
     if (boundary != o.boundary) return boundary < o.boundary;
     if (annotations != o.annotations) return annotations < o.annotations;
     return stages < o.stages;
   }
 };
 
-Score score_of(const std::vector<Stage> &st) {
-  Score sc{0, 0, 0, 0, (int)st.size()};
+int64_t binom_i(int a, int b) {
+  if (b < 0 || a < 0 || b > a) return 0;
+  int64_t r = 1;
+  for (int i = 1; i <= b; i++) r = r * (a - b + i) / i;
+  return r;
+}
+
+// Engine-aware cost of the triangle and leaf blocks, in units of one table
+// entry joined per data edge: a triangle block joins, per data triangle and
+// for each of its six node assignments, the rows of all its annotating
+// blocks (their product of row lengths; four times that when two or more
+// annotate it, the partial-list form; twice when its output is keyed by
+// edge); a leaf block joins per data edge one row of each annotating block.
+// Data triangles are taken as three per edge, the order of the heavy-tailed
+// benchmark graphs (about 3.4 on the Chung-Lu n = 10^6 graph).
+double join_cost(const std::vector<Stage> &st, int k) {
+  auto row_len = [&](int c) -> double {
+    const Stage &b = st[c];
+    return (double)(b.nb == 2 ? binom_i(k - 2, b.s - 2) : binom_i(k - 1, b.s - 1));
+  };
+  double tot = 0.0;
+  for (auto &g : st) {
+    if (g.kind != ST_TRI && g.kind != ST_LEAF) continue;
+    const int ne = g.kind == ST_LEAF ? 1 : g.L;
+    double prod = 1.0;
+    int kids = 0;
+    for (int i = 0; i < g.L; i++)
+      if (g.node_child[i] >= 0) prod *= row_len(g.node_child[i]), kids++;
+    for (int i = 0; i < ne; i++)
+      if (g.edge_child[i] >= 0) prod *= row_len(g.edge_child[i]), kids++;
+    if (g.kind == ST_LEAF) tot += prod;
+    else tot += 3.0 * 6.0 * prod * (kids >= 2 ? 4.0 : 1.0) * (g.nb == 2 ? 2.0 : 1.0);
+  }
+  return tot;
+}
+
+Score score_of(const std::vector<Stage> &st, int k = 0, bool paper_only = false) {
+  Score sc{0, 0, 0.0, 0, 0, (int)st.size(), paper_only};
   for (auto &g : st) {
     if (g.kind == ST_CYCLE_NONROOT) sc.unsupported = 1;
     if (g.kind == ST_CYCLE_ROOT && g.L > kMaxCycle) sc.unsupported = 1;
@@ -261,6 +305,7 @@ Score score_of(const std::vector<Stage> &st) {
     for (int i = 0; i < g.L; i++) sc.annotations += g.node_child[i] >= 0;
     for (int i = 0; i < ne; i++) sc.annotations += g.edge_child[i] >= 0;
   }
+  if (k > 0 && !paper_only) sc.cost = join_cost(st, k);
   return sc;
 }
 
@@ -346,7 +391,7 @@ int64_t count_automorphisms(int k, const std::vector<std::pair<int, int>> &edges
   return count;
 }
 
-int plan_query(int k, const std::vector<std::pair<int, int>> &edges, Plan &out) {
+int plan_query(int k, const std::vector<std::pair<int, int>> &edges, Plan &out, bool paper_only) {
   int rc = validate(k, edges);
   if (rc != CC_OK) return rc;
   QS s0;
@@ -364,7 +409,7 @@ int plan_query(int k, const std::vector<std::pair<int, int>> &edges, Plan &out) 
     if (try_root(s, st, &ok)) {
       if (ok) {
         explored++;
-        Score sc = score_of(st);
+        Score sc = score_of(st, k, paper_only);
         if (!found || sc < best) { best = sc; best_st = st; found = true; }
       }
       st.resize(mark);
@@ -404,10 +449,13 @@ int plan_query(int k, const std::vector<std::pair<int, int>> &edges, Plan &out) 
 int plan_enumerate(int k, const std::vector<std::pair<int, int>> &edges, std::vector<PlanChoice> &out) {
   int rc = validate(k, edges);
   if (rc != CC_OK) return rc;
-  Plan def;
-  int drc = plan_query(k, edges, def);
+  Plan def, pap;
+  int drc = plan_query(k, edges, def, false);
+  int prc = plan_query(k, edges, pap, true);
   const std::string def_sig = (drc == CC_OK || drc == CC_ERR_UNSUPPORTED) && !def.stages.empty()
                                   ? def.stages.back().sig : std::string();
+  const std::string pap_sig = (prc == CC_OK || prc == CC_ERR_UNSUPPORTED) && !pap.stages.empty()
+                                  ? pap.stages.back().sig : std::string();
   QS s0;
   init_state(s0, k, edges);
   std::map<std::string, size_t> seen;
@@ -432,12 +480,14 @@ int plan_enumerate(int k, const std::vector<std::pair<int, int>> &edges, std::ve
             c.seq.push_back(g.kind == ST_LEAF ? 0 : g.L);
             for (int j = 0; j < g.L; j++) c.seq.push_back(g.nodes[j]);
           }
-          Score sc = score_of(p.stages);
+          Score sc = score_of(p.stages, k);
           c.supported = sc.unsupported == 0;
           c.longest = sc.longest;
           c.boundary = sc.boundary;
           c.annotations = sc.annotations;
+          c.cost = sc.cost;
           c.is_default = sig == def_sig;
+          c.is_paper = sig == pap_sig;
           seen[sig] = out.size();
           out.push_back(c);
         }

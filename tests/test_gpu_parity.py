@@ -310,10 +310,16 @@ def test_per_vertex_split_matches_oracle(cc, qname):
         cols = O.colors(11, 0, g.n, k)
         expect, _, per = O.dp_count(g, k, e, cols, per_source=True)
         assert total == expect == int(pv.sum())
-        info = P.cc_query_info(cc.h, qid)
-        # the split is by the root block: compare when the oracle's root is the same kind
+        # the split is by the root block: compare when the library's and the
+        # oracle's roots are the same block (same kind, same query nodes)
         blocks, root, _ = O.decompose(k, e)
-        if blocks[root]["kind"] == "root_cycle" and info["longest_cycle"] >= 3 and qname not in ("glasses",):
+        lib_blocks, _ = P.cc_plan_inspect(k, e)
+        lib_root = lib_blocks[-1]
+        same = (lib_root["kind"] in ("root_cycle", "triangle") and blocks[root]["kind"] == "root_cycle"
+                and sorted(lib_root["nodes"]) == sorted(blocks[root]["nodes"]))
+        same = same or (lib_root["kind"] == "root_node" and blocks[root]["kind"] == "root_node"
+                        and lib_root["nodes"] == blocks[root]["nodes"])
+        if same:
             assert [int(x) for x in pv] == per
     finally:
         cc.free_graph(gid)

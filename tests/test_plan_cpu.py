@@ -109,3 +109,33 @@ def test_default_plans_of_workload_queries_are_supported():
         k, e = QUERIES[name]
         blocks, _ = P.cc_plan_inspect(k, e)
         assert all(b["kind"] != "cycle" for b in blocks)
+
+
+def test_tree_enumeration_and_ranking():
+    # every decomposition tree (Section 5.3) once; the paper's heuristic picks
+    # the least by (longest cycle, boundary nodes, annotations), the library
+    # the least by (longest cycle, join cost, boundary nodes, annotations)
+    import paper_1602_04478_gb300 as P
+    shapes = {
+        "chord_pendant": gg.query("chord_pendant"),
+        "diamond": gg.query("diamond"),
+        "bowtie_pendants": (7, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 2), (0, 5), (4, 6)]),
+        "C6_2pendants": gg.query("C6_2pendants"),
+    }
+    counts = {"chord_pendant": 4, "diamond": 2, "bowtie_pendants": 28, "C6_2pendants": 11}
+    for name, (k, e) in shapes.items():
+        trees = P.cc_plan_enumerate(k, e)
+        assert len(trees) == counts[name], name
+        assert len({tuple(t["seq"]) for t in trees}) == len(trees)
+        sup = [t for t in trees if t["supported"]]
+        paper = [t for t in sup if t["paper"]]
+        lib = [t for t in sup if t["default"]]
+        assert len(paper) == 1 and len(lib) == 1, name
+        pk = lambda t: (t["longest"], t["boundary"], t["annotations"])
+        lk = lambda t: (t["longest"], t["cost"], t["boundary"], t["annotations"])
+        assert pk(paper[0]) == min(pk(t) for t in sup)
+        assert lk(lib[0]) == min(lk(t) for t in sup)
+        # the default plan is that tree
+        blocks, _ = P.cc_plan_inspect(k, e)
+        again, _ = P.cc_plan_inspect(k, e, lib[0]["seq"]) if lib[0]["seq"] else (blocks, 0)
+        assert blocks == again, name
