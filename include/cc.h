@@ -53,6 +53,7 @@ extern "C" {
 #define CC_ERR_CUDA (-8)         /* a CUDA runtime call failed                 */
 #define CC_ERR_UNSUPPORTED (-9)  /* the query needs a block kind not built    */
 #define CC_ERR_NOT_CONNECTED (-10) /* the query graph is not connected         */
+#define CC_ERR_BOUNDS (-11)      /* an index left its array (bounds-check build only) */
 
 #define CC_MAX_K 12
 

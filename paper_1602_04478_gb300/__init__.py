@@ -26,7 +26,7 @@ CC_OK = 0
 ERRORS = {
     -1: "CC_ERR_INVALID_ARG", -2: "CC_ERR_BAD_GRAPH", -3: "CC_ERR_NOT_TW2", -4: "CC_ERR_K_RANGE",
     -5: "CC_ERR_OOM", -6: "CC_ERR_OVERFLOW", -7: "CC_ERR_TIMEOUT", -8: "CC_ERR_CUDA",
-    -9: "CC_ERR_UNSUPPORTED", -10: "CC_ERR_NOT_CONNECTED",
+    -9: "CC_ERR_UNSUPPORTED", -10: "CC_ERR_NOT_CONNECTED", -11: "CC_ERR_BOUNDS",
 }
 EXPORTED = [
     "cc_create", "cc_destroy", "cc_set_allocator", "cc_set_memory_budget", "cc_set_heavy_degree",

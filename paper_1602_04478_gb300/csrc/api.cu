@@ -356,6 +356,7 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
 }
 
 int status_code(const u64 *st) {
+  if (st[ST_BOUNDS]) return CC_ERR_BOUNDS;
   if (st[ST_TIMEOUT] & 1ull) return CC_ERR_TIMEOUT;
   if (st[ST_TIMEOUT] & 2ull) return CC_ERR_UNSUPPORTED;
   if (st[ST_OVERFLOW]) return CC_ERR_OVERFLOW;
@@ -403,6 +404,7 @@ const char *cc_strerror(int code) {
     case CC_ERR_CUDA: return "CUDA runtime error";
     case CC_ERR_UNSUPPORTED: return "query needs a block kind without a kernel (non-root cycle longer than 3, or root cycle longer than 8)";
     case CC_ERR_NOT_CONNECTED: return "query graph is not connected";
+    case CC_ERR_BOUNDS: return "an index left its array (bounds-check build)";
     default: return "unknown error";
   }
 }

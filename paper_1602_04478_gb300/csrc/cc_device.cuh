@@ -83,9 +83,25 @@ __device__ __forceinline__ unsigned long long warp_sum_ck(unsigned long long v, 
 
 // status words in device memory
 // ST_SCAN0 + j: data edges scanned out of level j of a root cycle's halves
-// (structural counting only; a status block then has kStatusWords words)
-enum { ST_COUNT = 0, ST_OVERFLOW = 1, ST_TIMEOUT = 2, ST_BADGRAPH = 3, ST_UNITS = 4, ST_MAXDEG = 5, ST_SCAN0 = 8 };
+// (structural counting only; a status block then has kStatusWords words).
+// ST_BOUNDS: an index outside its array (bounds-check build only).
+enum { ST_COUNT = 0, ST_OVERFLOW = 1, ST_TIMEOUT = 2, ST_BADGRAPH = 3, ST_UNITS = 4, ST_MAXDEG = 5, ST_BOUNDS = 6,
+       ST_SCAN0 = 8 };
 constexpr int kStatusWords = 16;
+
+// Bounds-check build (libcc_boundscheck.so, CC_BOUNDS_CHECK set): an index
+// read from data (CSR entries, lists, local indices, triangle records)
+// outside its array sets status[ST_BOUNDS] and the access is skipped.  In
+// the normal build the check compiles away.
+#ifdef CC_BOUNDS_CHECK
+__device__ __forceinline__ bool cc_in(int64_t i, int64_t size, unsigned long long *status) {
+  if (i >= 0 && i < size) return true;
+  atomicOr(status + ST_BOUNDS, 1ull);
+  return false;
+}
+#else
+__device__ __forceinline__ bool cc_in(int64_t, int64_t, unsigned long long *) { return true; }
+#endif
 
 __device__ __forceinline__ void flag_overflow(unsigned long long *status, unsigned ovf) {
   if (ovf) atomicOr(status + ST_OVERFLOW, 1ull);

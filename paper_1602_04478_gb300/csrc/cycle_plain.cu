@@ -43,6 +43,8 @@ constexpr int kTagShift = 29;
 constexpr uint32_t kTagMask = (1u << kTagShift) - 1u;
 
 struct PcScratch {
+  int64_t n;                   // vertices (bounds-check build)
+  u64 *status;                 // status block of the pass (bounds-check build)
   uint16_t *w2;                // [n][32 sources][8 colours] level-2 rows (u16: max degree < 65536)
   unsigned long long *member;  // [n]: bit b level 1 of source b, bit 32+b level 2 (b < 32)
   uint32_t *anym;              // [(n + 31) / 32]: bit w set when w is in some level the pull reads
@@ -64,7 +66,7 @@ struct PcGroup {
 // once per source, the warp taking its list slots with one atomic.
 template <int L>
 __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uint8_t *colors, PcScratch SA,
-                                                          PcGroup GA, PcScratch SB, PcGroup GB) {
+                                                          PcGroup GA, PcScratch SB, PcGroup GB, u64 *status) {
   constexpr unsigned FULL = 0xffffffffu;
   // rows 0 .. GA.B-1 of the grid serve group A (bank A), the rest group B
   const bool second = (int)blockIdx.y >= GA.B;
@@ -82,6 +84,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uin
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp0; i < du; i += nwarps) {
     const int32_t v = __ldg(g.col + ub + i);
+    if (!cc_in(v, u, status)) continue;
     const int cv = colors[v];
     if (cv == cu) continue;
     if (L <= 5 && lane == 0) {
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uin
       const int32_t w = e < vend ? __ldg(g.col + e) : INT32_MAX;
       const bool done = __any_sync(FULL, w >= u);
       bool need = false;
-      if (w < u) {
+      if (w < u && cc_in(w, n, status)) {
         const int cw = colors[w];
         if (cw != cu && cw != cv) {
           // 16-bit counter inside a 32-bit word; counts stay below 2^16 (host check)
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uin
         int base = 0;
         if (lane == leader) base = atomicAdd(S.cnt + b, __popc(nb));
         base = __shfl_sync(FULL, base, leader);
-        if (need) S.list[(int64_t)b * n + base + __popc(nb & lt)] = w;
+        if (need && cc_in(base + __popc(nb & lt), n, status)) S.list[(int64_t)b * n + base + __popc(nb & lt)] = w;
       }
       if (done) break;
     }
@@ -133,7 +136,8 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels(GraphView g, const uin
 // clear are never read, so rows left from the previous group need no
 // clearing; the pass as a whole zeroes its scratch once it switches back to
 // the push form or ends.
-__global__ void k_pc_mark1(GraphView g, const uint8_t *colors, PcScratch S, PcGroup G, bool level1_read) {
+__global__ void k_pc_mark1(GraphView g, const uint8_t *colors, PcScratch S, PcGroup G, bool level1_read,
+                           u64 *status) {
   const int b = blockIdx.y;
   const int32_t u = G.u[b];
   const int cu = colors[u];
@@ -141,6 +145,7 @@ __global__ void k_pc_mark1(GraphView g, const uint8_t *colors, PcScratch S, PcGr
   const int du = g.lo_cnt[u];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < du; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = __ldg(g.col + ub + i);
+    if (!cc_in(v, u, status)) continue;
     if (colors[v] != cu) {
       atomicOr(S.member + v, 1ull << b);
       if (level1_read) atomicOr(S.anym + (v >> 5), 1u << (v & 31));
@@ -165,7 +170,7 @@ __device__ __forceinline__ void pc_count(uint32_t (&cnt)[L], int c, uint32_t v) 
 // bank, in one pass over the vertices w (the scan of N(w) is shared).
 template <int L, int NG>
 __global__ void __launch_bounds__(kPcThreads) k_pc_levels_pull(GraphView g, const uint8_t *colors, PcScratch SA,
-                                                               PcGroup GA, PcScratch SB, PcGroup GB) {
+                                                               PcGroup GA, PcScratch SB, PcGroup GB, u64 *status) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, b = lane;
   bool active[NG];
@@ -203,7 +208,8 @@ __global__ void __launch_bounds__(kPcThreads) k_pc_levels_pull(GraphView g, cons
       const int deg = (int)(g.row[w + 1] - wb);
       for (int base = 0; base < deg; base += 32) {
         const int j = base + lane;
-        const int32_t vl = j < deg ? __ldg(g.col + wb + j) : INT32_MAX;
+        int32_t vl = j < deg ? __ldg(g.col + wb + j) : INT32_MAX;
+        if (vl < umax && !cc_in(vl, g.n, status)) vl = INT32_MAX;
         const bool past = __any_sync(FULL, vl >= umax);
         uint32_t ml[NG];
         uint32_t mor = 0u;
@@ -333,6 +339,8 @@ __device__ __forceinline__ PcChunk pc_load_chunk(const uint32_t *tag, const PcSc
   PcChunk k;
   const uint32_t t = j < deg ? __ldg(tag + xb + j) : 0xFFFFFFFFu;
   k.w = j < deg ? (int32_t)(t & kTagMask) : INT32_MAX;
+  // a tagged neighbour below the group's highest source is a vertex id
+  if (k.w < umax && !cc_in(k.w, S.n, S.status)) k.w = INT32_MAX;
   k.c = k.w < umax ? (int)(t >> kTagShift) : cx;
   const bool any = k.c != cx && ((__ldg(S.anym + (k.w >> 5)) >> (k.w & 31)) & 1u);
   k.m = any ? __ldg(S.member + k.w) : 0ull;
@@ -534,6 +542,7 @@ __global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull2(GraphView g, const u
     const uint32_t t = lane < deg ? __ldg(tag + xb + lane) : 0xFFFFFFFFu;
     PcChunk kA;
     kA.w = lane < deg ? (int32_t)(t & kTagMask) : INT32_MAX;
+    if (kA.w < umax && !cc_in(kA.w, g.n, status)) kA.w = INT32_MAX;
     kA.c = kA.w < umax ? (int)(t >> kTagShift) : cx;
     const bool any = kA.c != cx && ((__ldg(SA.anym + (kA.w >> 5)) >> (kA.w & 31)) & 1u);
     kA.m = any ? __ldg(SA.member + kA.w) : 0ull;
@@ -551,7 +560,7 @@ __global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull2(GraphView g, const u
 // grid.y = source b: zero its level-1 membership words and, for its listed
 // level-2 vertices, the membership word, the row and the list entry.
 template <int L>
-__global__ void k_pc_clear(GraphView g, PcScratch SA, PcGroup GA, PcScratch SB, PcGroup GB) {
+__global__ void k_pc_clear(GraphView g, PcScratch SA, PcGroup GA, PcScratch SB, PcGroup GB, u64 *status) {
   // rows 0 .. GA.B-1 of the grid serve group A (bank A), the rest group B
   const bool second = (int)blockIdx.y >= GA.B;
   const PcScratch S = second ? SB : SA;
@@ -563,12 +572,16 @@ __global__ void k_pc_clear(GraphView g, PcScratch SA, PcGroup GA, PcScratch SB, 
   const int32_t u = G.u[b];
   const int64_t ub = g.row[u];
   const int du = g.lo_cnt[u];
-  for (int64_t i = t0; i < du; i += nt) S.member[__ldg(g.col + ub + i)] = 0;
+  for (int64_t i = t0; i < du; i += nt) {
+    const int32_t v = __ldg(g.col + ub + i);
+    if (cc_in(v, n, status)) S.member[v] = 0;
+  }
   if (L >= 5) {
     const int cnt = S.cnt[b];
     for (int64_t i = t0; i < cnt; i += nt) {
       const int32_t w = S.list[(int64_t)b * n + i];
       S.list[(int64_t)b * n + i] = 0;
+      if (!cc_in(w, n, status)) continue;
       S.member[w] = 0;
       *(uint4 *)(S.w2 + ((int64_t)w * kPcMaxB + b) * 8) = make_uint4(0, 0, 0, 0);
     }
@@ -691,6 +704,7 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
       // chunk that reaches u.
       for (int i = wib; i < du; i += NW) {
         const int32_t v = __ldg(g.col + ub + i);
+        if (!cc_in(v, u, status)) continue;
         const int cv = colors[v];
         if (cv == cu) continue;
         const int64_t vb = g.row[v], vend = g.row[v + 1];
@@ -698,11 +712,11 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
           const int64_t e = e0 + lane;
           const int32_t w = e < vend ? __ldg(g.col + e) : INT32_MAX;
           const bool done = __any_sync(FULL, w >= u);
-          if (w < u) {
+          if (w < u && cc_in(w, g.n, status)) {
             const int cw = colors[w];
             if (cw != cu && cw != cv) {
               const int iw = pl_index(id2, w, L2, &s_n2, tmo);
-              if (iw >= 0) atomicAdd(W2 + (int64_t)iw * 8 + cv, 1u);
+              if (iw >= 0 && cc_in(iw, g.n, status)) atomicAdd(W2 + (int64_t)iw * 8 + cv, 1u);
             }
           }
           if (done) break;
@@ -715,6 +729,7 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
         // row added into x's pair row
         for (int i = wib; i < n2; i += NW) {
           const int32_t w = L2[i];
+          if (!cc_in(w, g.n, status)) continue;
           const int cw = colors[w];
           const uint4 r0 = *(const uint4 *)(W2 + (int64_t)i * 8);
           const uint4 r1 = *(const uint4 *)(W2 + (int64_t)i * 8 + 4);
@@ -724,7 +739,7 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
             const int64_t e = e0 + lane;
             const int32_t x = e < wend ? __ldg(g.col + e) : INT32_MAX;
             const bool done = __any_sync(FULL, x >= u);
-            if (x < u) {
+            if (x < u && cc_in(x, g.n, status)) {
               const int cx = colors[x];
               if (cx != cu && cx != cw) {
                 bool any = false;
@@ -732,7 +747,7 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
                 for (int c = 0; c < 8; c++) any = any || (row[c] != 0u && c != cx);
                 if (any) {
                   const int ix = pl_index(id3, x, L3, &s_n3, tmo);
-                  if (ix >= 0) {
+                  if (ix >= 0 && cc_in(ix, g.n, status)) {
 #pragma unroll
                     for (int c = 0; c < 8; c++) {
                       const uint32_t t = row[c];
@@ -752,6 +767,7 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
       u64 mine = 0;
       for (int i = tid; i < nx; i += kPlThreads) {
         const int32_t x = L >= 5 ? L3[i] : L2[i];
+        if (!cc_in(x, g.n, status)) continue;
         const int cx = colors[x];
         const uint32_t fm = ((1u << k) - 1u) & ~((1u << cu) | (1u << cx));
         int f[4];
@@ -768,7 +784,7 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
         } else if (L == 5) {
           const uint32_t *w3 = W3 + (int64_t)i * 16;
           const int ix = id2[x];  // x's level-2 row (paths u-v-x), if x was reached at level 2
-          if (ix > 0) {
+          if (ix > 0 && cc_in(ix - 1, g.n, status)) {
             const uint32_t *w2 = W2 + (int64_t)(ix - 1) * 8;
             u64 t = mul_ck((u64)w2[f[0]], (u64)w3[pair_idx(f[1], f[2])], ovf);
             t = add_ck(t, mul_ck((u64)w2[f[1]], (u64)w3[pair_idx(f[0], f[2])], ovf), ovf);
@@ -792,14 +808,14 @@ __global__ void __launch_bounds__(kPlThreads) k_pc_light(GraphView g, const uint
       // everything back to zero: rows by local index, ids through the lists
       if (L >= 5) {
         for (int i = tid; i < s_n3; i += kPlThreads) {
-          id3[L3[i]] = 0;
+          if (cc_in(L3[i], g.n, status)) id3[L3[i]] = 0;
           L3[i] = 0;
           uint4 *z = (uint4 *)(W3 + (int64_t)i * 16);
           z[0] = z[1] = z[2] = z[3] = make_uint4(0, 0, 0, 0);
         }
       }
       for (int i = tid; i < n2; i += kPlThreads) {
-        id2[L2[i]] = 0;
+        if (cc_in(L2[i], g.n, status)) id2[L2[i]] = 0;
         L2[i] = 0;
         uint4 *z = (uint4 *)(W2 + (int64_t)i * 8);
         z[0] = z[1] = make_uint4(0, 0, 0, 0);
@@ -970,12 +986,12 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
     const int64_t du = c.cur_graph_row[G.umax + 1] - c.cur_graph_row[G.umax];
     dim3 gl((unsigned)std::max<int64_t>(1, std::min<int64_t>(sms * 2, (du * 32 + kPcThreads - 1) / kPcThreads)),
             G.B + G2.B);
-    k_pc_levels<L><<<gl, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G, S1, G2);
+    k_pc_levels<L><<<gl, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G, S1, G2, a.status);
     c.kernels++;
   };
   // scratch of one group (bank 0) or two back to zero; totals into the count
   auto close_groups = [&](const PcGroup &G, const PcGroup &G2) {
-    k_pc_clear<L><<<dim3(std::max(1, sms / 8), G.B + G2.B), 256, 0, c.stream>>>(a.g, S0, G, S1, G2);
+    k_pc_clear<L><<<dim3(std::max(1, sms / 8), G.B + G2.B), 256, 0, c.stream>>>(a.g, S0, G, S1, G2, a.status);
     c.kernels++;
     k_pc_finish<<<1, G2.B ? 64 : 32, 0, c.stream>>>(S0, G, S1, G2, a.multiplier, a.per_vertex, a.status);
     c.kernels++;
@@ -1011,13 +1027,13 @@ static int run_plain_L(Ctx &c, const CycleArgs &a, int32_t first_rank, const PcS
         const PcGroup &Gq = q == 0 ? G : G2;
         const int64_t du = c.cur_graph_row[Gq.umax + 1] - c.cur_graph_row[Gq.umax];
         dim3 gm((unsigned)std::max<int64_t>(1, std::min<int64_t>(sms, (du + kPcThreads - 1) / kPcThreads)), Gq.B);
-        k_pc_mark1<<<gm, kPcThreads, 0, c.stream>>>(a.g, a.colors, q == 0 ? S0 : S1, Gq, L <= 5);
+        k_pc_mark1<<<gm, kPcThreads, 0, c.stream>>>(a.g, a.colors, q == 0 ? S0 : S1, Gq, L <= 5, a.status);
         c.kernels++;
       }
       if (two)
-        k_pc_levels_pull<L, 2><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G, S1, G2);
+        k_pc_levels_pull<L, 2><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G, S1, G2, a.status);
       else
-        k_pc_levels_pull<L, 1><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G, S0, G);
+        k_pc_levels_pull<L, 1><<<sms * 4, kPcThreads, 0, c.stream>>>(a.g, a.colors, S0, G, S0, G, a.status);
       c.kernels++;
       timing_end(c);
       // dense members: each group pulled on its own (the shared scan is a
@@ -1093,6 +1109,8 @@ int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank) {
   char *base = (char *)c.hv_scratch;
   PcScratch S[2];
   for (int k = 0; k < 2; k++) {
+    S[k].n = n;
+    S[k].status = a.status;
     S[k].w2 = (uint16_t *)(base + o_w2[k]);
     S[k].member = (unsigned long long *)(base + o_mem[k]);
     S[k].list = (int32_t *)(base + o_list[k]);

@@ -16,6 +16,8 @@
 //
 // Root singleton (Section 5.2, last paragraph): sum the annotating block's
 // table over all vertices (its rows hold the single full signature).
+#include <algorithm>
+
 #include "cc_kernels.h"
 
 namespace cc {
@@ -94,7 +96,96 @@ __global__ void __launch_bounds__(256) k_leaf_join(LeafArgs a) {
   flag_overflow(a.status, ovf);
 }
 
+// The same join for a leaf block with no edge table (the edge is a plain data
+// edge), one warp per vertex x with the lanes over the (neighbour, B-row
+// entry) pairs of x: consecutive lanes read consecutive entries of a
+// neighbour's row, so the gather is coalesced, and the signature arithmetic
+// is one lookup in a table built per block in shared memory:
+//   slot[(cx k + cy) RB + j] = the slot of S_B(j) u {cx} in x's Y row, or -1
+//   when S_B(j) holds cx (the signatures would overlap beyond chi(y)).
+// Without a B table the neighbour's row is the single signature {cy}.
+constexpr int kFlatMaxTable = 8192;
+
+__global__ void __launch_bounds__(256) k_leaf_join_flat(LeafArgs a) {
+  extern __shared__ __align__(16) unsigned char flat_smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int k = a.k;
+  const int RB = a.B.p ? a.B.R : 1;
+  const int sB = a.B.p ? a.B.s : 1;
+  u64 *Y = reinterpret_cast<u64 *>(flat_smem) + (size_t)wib * a.RY;
+  int16_t *tbl = reinterpret_cast<int16_t *>(reinterpret_cast<u64 *>(flat_smem) + (size_t)8 * a.RY);
+  for (int t = threadIdx.x; t < k * k * RB; t += blockDim.x) {
+    const int j = t % RB, cy = (t / RB) % k, cx = t / (RB * k);
+    const uint32_t mB = a.B.p ? umask(a.lut, sB, j, cy) : (1u << cy);
+    tbl[t] = (cx == cy || (mB >> cx & 1u)) ? (int16_t)-1 : (int16_t)uslot(a.lut, mB | (1u << cx), cx);
+  }
+  __syncthreads();
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  // this lane's starting (neighbour, entry) pair and its step per pass
+  const int i0 = lane / RB, j0 = lane % RB, di = 32 / RB, dj = 32 % RB;
+  unsigned ovf = 0;
+  for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + wib; x < a.g.n; x += nwarps) {
+    const int cx = a.colors[x];
+    for (int i = lane; i < a.RY; i += 32) Y[i] = 0;
+    __syncwarp();
+    const int64_t rb = a.g.row[x];
+    const int deg = (int)(a.g.row[x + 1] - rb);
+    const int16_t *tx = tbl + (size_t)cx * k * RB;
+    for (int i = i0, j = j0; i < deg;) {
+      const int32_t y = __ldg(a.g.col + rb + i);
+      const bool ok = cc_in(y, a.g.n, a.status);
+      const int cy = ok ? a.colors[y] : 0;
+      const u64 v = !ok ? 0ull : (a.B.p ? __ldg(a.B.p + (int64_t)y * RB + j) : 1ull);
+      const int slot = tx[cy * RB + j];
+      if (v && cc_in(slot, a.RY, a.status)) {
+        const unsigned long long old = atomicAdd(Y + slot, v);
+        ovf |= (old + v < old);
+      }
+      i += di;
+      j += dj;
+      if (j >= RB) j -= RB, i++;
+    }
+    __syncwarp();
+    u64 *orow = a.out + x * (int64_t)a.R_out;
+    if (!a.A.p) {
+      for (int o = lane; o < a.R_out; o += 32) orow[o] = Y[o];
+    } else {
+      const u64 *arow = a.A.p + x * (int64_t)a.A.R;
+      for (int o = lane; o < a.R_out; o += 32) {
+        uint32_t mO = umask(a.lut, a.s_out, o, cx);
+        u64 acc = 0;
+        for (int ja = 0; ja < a.A.R; ja++) {
+          u64 vA = __ldg(arow + ja);
+          if (!vA) continue;
+          uint32_t mA = umask(a.lut, a.A.s, ja, cx);
+          if (mA & ~mO) continue;
+          uint32_t mY = (mO & ~mA) | (1u << cx);
+          u64 vY = Y[uslot(a.lut, mY, cx)];
+          if (!vY) continue;
+          acc = add_ck(acc, mul_ck(vA, vY, ovf), ovf);
+        }
+        orow[o] = acc;
+      }
+    }
+    __syncwarp();
+  }
+  flag_overflow(a.status, ovf);
+}
+
 int launch_leaf(Ctx &c, const LeafArgs &a) {
+  const int RB = a.B.p ? a.B.R : 1;
+  if (!a.E.p && a.k * a.k * RB <= kFlatMaxTable) {
+    const size_t smem = (size_t)8 * a.RY * sizeof(u64) + (size_t)a.k * a.k * RB * sizeof(int16_t);
+    if (smem > 200 * 1024) return CC_ERR_UNSUPPORTED;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_leaf_join_flat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int64_t blocks = std::min<int64_t>(std::max<int64_t>((a.g.n + 7) / 8, 1), 152 * 8);
+    timing_begin(c, "leaf_join");
+    k_leaf_join_flat<<<(unsigned)blocks, 256, smem, c.stream>>>(a);
+    c.kernels++;
+    timing_end(c);
+    return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+  }
   size_t smem = (size_t)8 * a.RY * sizeof(u64);
   if (smem > 200 * 1024) return CC_ERR_UNSUPPORTED;
   if (smem > 48 * 1024)

@@ -705,12 +705,15 @@ __global__ void __launch_bounds__(kEmitThreads) k_tl_emit(TriArgs a, TriMode md,
     const int64_t t1 = min(a.n_tri, t0 + kEmitTile);
     for (int64_t i = t0 + tid; i < t1; i += blockDim.x) {
       const int32_t u = __ldg(a.tri_u + i), v = __ldg(a.tri_v + i), w = __ldg(a.tri_w + i);
+      if (!cc_in(u, a.g.n, a.status) || !cc_in(v, u, a.status) || !cc_in(w, v, a.status)) continue;
       const int cu = a.colors[u], cv = a.colors[v], cw = a.colors[w];
       if (cu == cv || cu == cw || cv == cw) continue;
       u64 r = 0;
       const int64_t p01 = md.need_pos ? __ldg(a.tri_p + i) : 0;
       const int64_t p02 = md.need_pos ? __ldg(a.tri_p + a.n_tri + i) : 0;
       const int64_t p12 = md.need_pos ? __ldg(a.tri_p + 2 * a.n_tri + i) : 0;
+      if (!cc_in(p01, a.g.nnz, a.status) || !cc_in(p02, a.g.nnz, a.status) || !cc_in(p12, a.g.nnz, a.status))
+        continue;
       tri_visit<kForm>(a, md, sk, u, v, w, cu, cv, cw, p01, p02, p12, r, ovf);
       if (a.nb == 0 && r) {
         if (u == u0) {
