@@ -626,7 +626,11 @@ __global__ void k_pc_finish(PcScratch SA, PcGroup GA, PcScratch SB, PcGroup GB, 
 // from the swap's old value (or, in the short window before the winner
 // publishes, waits for it, with an iteration limit that reports
 // CC_ERR_TIMEOUT), and then adds into v's row.
-constexpr int kPlThreads = 256;
+#ifndef CC_PL_THREADS
+#define CC_PL_THREADS 256
+#endif
+constexpr int kPlThreads = CC_PL_THREADS;      // threads per source (one CTA)
+constexpr int kPlSlotsPerSM = 1024 / kPlThreads;  // resident CTAs per SM, one scratch slot each
 
 __device__ __forceinline__ int pair_idx(int a, int b) {
   int hi = a > b ? a : b, lo = a > b ? b : a;
@@ -872,7 +876,7 @@ int run_plain_light(Ctx &c, const CycleArgs &a, int32_t end_rank) {
   // take at most a quarter of the free device memory and 64 GiB.  A scratch
   // already large enough for more slots is used whole, and under stream
   // capture only the scratch at hand is used (no allocation).
-  constexpr int kMaxSlots = 152 * 4;
+  constexpr int kMaxSlots = 152 * kPlSlotsPerSM;
   const size_t have = c.scratch_bytes > 256 ? (c.scratch_bytes - 256) / std::max<size_t>(1, S.slot_bytes) : 0;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(c.stream, &cs) != cudaSuccess) return CC_ERR_CUDA;
