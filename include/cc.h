@@ -213,6 +213,14 @@ typedef struct cc_request {
 int cc_count_batch(cc_ctx *ctx, const cc_request *reqs, int n_reqs, uint64_t *colorful, int *status);
 /* Whether cc_count_batch records and replays CUDA graphs (default 1). */
 int cc_set_graph_capture(cc_ctx *ctx, int enable);
+/* Lanes of cc_count_batch (1..4, default 2): the batch's passes are dealt
+ * out round-robin to this context and lanes - 1 auxiliary contexts, each
+ * with its own CUDA stream, scratch and tables and sharing this context's
+ * graphs and plans, so passes of different colourings run concurrently
+ * (each lane's scratch is allocated like this context's).  A batch on a
+ * graph with explicit colours (cc_set_colors) uses one lane.  Counts do not
+ * depend on the lanes. */
+int cc_set_batch_lanes(cc_ctx *ctx, int lanes);
 /* Time the root-cycle closure of query_id on graph_id for heavy-source
  * degree thresholds 64, 96, 128, 192, ..., 3072, 4096 (steps of 1.5 and 4/3,
  * up to twice the maximum degree) on one colouring, after one untimed run,

@@ -431,11 +431,13 @@ void cc_destroy(cc_ctx *ctx) {
   Ctx &c = ctx->c;
   cudaSetDevice(c.device);
   cudaStreamSynchronize(c.stream);
+  batch_cache_clear(c);
+  for (auto *l : c.lanes) cc_destroy(l);  // batch lanes borrow this context's graphs
+  c.lanes.clear();
   for (auto &g : c.graphs) graph_free(c, g.second);
   dev_free(c, c.scratch, c.scratch_bytes);
   dev_free(c, c.hv_scratch, c.hv_scratch_bytes);
   dev_free(c, c.tag_scratch, c.tag_scratch_bytes);
-  batch_cache_clear(c);
   dev_free(c, c.lut_rank, 4096 * 2);
   dev_free(c, c.lut_unrank, 13 * kUnrankStride * 2);
   dev_free(c, c.d_status, kStatusWords * sizeof(u64));

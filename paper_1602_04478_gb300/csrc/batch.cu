@@ -8,6 +8,14 @@
 // instantiated graph: one launch for all passes, no per-pass host work.  The
 // kernels leave their scratch zeroed, so a replay needs no clearing.
 //
+// Lanes: the passes of a batch are dealt out round-robin to `batch_lanes`
+// lanes -- this context and auxiliary contexts, each on its own stream with
+// its own scratch and tables, sharing this context's graphs and plans -- so
+// passes of different colourings run concurrently (one lane's memory-bound
+// per-CTA push beside another's issue-bound pulls, the small launches of one
+// filling the gaps of another).  Every lane forks from this context's stream
+// and joins it again; in the captured graph the lanes are parallel branches.
+//
 // The autotuner times the root-cycle closure for a few heavy/light degree
 // thresholds on one colouring and keeps the fastest for the (graph, query).
 #include <algorithm>
@@ -21,17 +29,21 @@ namespace cc {
 
 struct Ctx::BatchCache {
   std::vector<PassBuffers> bufs;  // one per request (its trials reuse them in order)
+  std::vector<std::vector<PassBuffers>> lane_bufs;  // the same for each other lane
   std::vector<int32_t> graph_of;  // graph of each request (for freeing)
   u64 *results = nullptr;         // [total trials][8] status words
   size_t total = 0;
   cudaGraphExec_t exec = nullptr;
   uint64_t kernels = 0;           // kernels one replay launches
+  cudaEvent_t fork = nullptr;     // this context's stream -> the lanes
+  std::vector<cudaEvent_t> join;  // each lane -> this context's stream
 };
 
 void batch_cache_clear(Ctx &c) {
   if (c.batches.empty()) return;
   cudaStreamSynchronize(c.stream);
   if (c.own_stream) cudaStreamSynchronize(c.own_stream);
+  for (auto *l : c.lanes) cudaStreamSynchronize(l->c.stream);
   for (auto &kv : c.batches) {
     Ctx::BatchCache *b = kv.second;
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -39,10 +51,61 @@ void batch_cache_clear(Ctx &c) {
       auto it = c.graphs.find(b->graph_of[i]);
       if (it != c.graphs.end()) free_pass(c, it->second, b->bufs[i]);
     }
+    for (size_t j = 0; j < b->lane_bufs.size() && j < c.lanes.size(); j++) {
+      Ctx &x = c.lanes[j]->c;
+      for (size_t i = 0; i < b->lane_bufs[j].size(); i++) {
+        auto it = x.graphs.find(b->graph_of[i]);
+        if (it != x.graphs.end()) free_pass(x, it->second, b->lane_bufs[j][i]);
+      }
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (auto e : b->join) cudaEventDestroy(e);
     dev_free(c, b->results, b->total * 8 * sizeof(u64));
     delete b;
   }
   c.batches.clear();
+}
+
+// The other lanes of a batch: created on first use, then brought up to date
+// with this context (graphs shared, never owned; plans, seed and settings
+// copied).  Returns the number of lanes usable for these requests.
+static int ready_lanes(Ctx &c, const cc_request *reqs, int n) {
+  int want = std::max(1, c.batch_lanes);
+  for (int i = 0; i < n; i++)
+    if (c.graphs[reqs[i].graph_id].colors) want = 1;  // explicit colours stay with this context
+  while ((int)c.lanes.size() < want - 1) {
+    cc_ctx *x = nullptr;
+    if (cc_create(&x, c.device, nullptr) != CC_OK) break;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      cc_destroy(x);
+      break;
+    }
+    x->c.stream = x->c.own_stream = st;
+    c.lanes.push_back(x);
+  }
+  const int lanes = std::min<int>(want, (int)c.lanes.size() + 1);
+  for (int j = 0; j < lanes - 1; j++) {
+    Ctx &x = c.lanes[j]->c;
+    x.budget = c.budget;
+    x.seed = c.seed;
+    x.heavy_degree = c.heavy_degree;
+    x.procedure = c.procedure;
+    x.tri_list = c.tri_list;
+    x.plans = c.plans;
+    for (auto &kv : c.graphs) {
+      DevGraph copy = kv.second;
+      copy.owned = false;
+      copy.colors = nullptr;
+      copy.colors_T = 0;
+      auto it = x.graphs.find(kv.first);
+      if (it != x.graphs.end() && copy.h_push_work.empty()) copy.h_push_work = it->second.h_push_work;
+      x.graphs[kv.first] = copy;
+    }
+    for (auto it = x.graphs.begin(); it != x.graphs.end();)
+      it = c.graphs.count(it->first) ? std::next(it) : x.graphs.erase(it);
+  }
+  return lanes;
 }
 
 }  // namespace cc
@@ -60,18 +123,37 @@ static std::string batch_key(const Ctx &c, const cc_request *reqs, int n) {
   return k;
 }
 
-// enqueue every (request, trial) pass of the batch on c.stream
+// enqueue every (request, trial) pass of the batch: pass number p goes to
+// lane p mod lanes; the lanes fork from c.stream and join it at the end
 static int enqueue_batch(Ctx &c, const cc_request *reqs, int n, Ctx::BatchCache &b) {
+  const int lanes = (int)b.lane_bufs.size() + 1;
+  if (lanes > 1) {
+    if (cudaEventRecord(b.fork, c.stream) != cudaSuccess) return CC_ERR_CUDA;
+    for (int j = 0; j < lanes - 1; j++)
+      if (cudaStreamWaitEvent(c.lanes[j]->c.stream, b.fork, 0) != cudaSuccess) return CC_ERR_CUDA;
+  }
+  std::vector<uint64_t> k0(lanes - 1);
+  for (int j = 0; j < lanes - 1; j++) k0[j] = c.lanes[j]->c.kernels;
   size_t slot = 0;
   for (int i = 0; i < n; i++) {
-    DevGraph &g = c.graphs[reqs[i].graph_id];
-    Plan &p = c.plans[reqs[i].query_id];
-    c.cur_tuned_heavy = g.tuned_heavy.count(reqs[i].query_id) ? g.tuned_heavy[reqs[i].query_id] : -1;
     for (int t = 0; t < reqs[i].trials; t++, slot++) {
-      int rc = enqueue_pass(c, g, p, (int64_t)reqs[i].first_trial + t, b.bufs[i], b.results + slot * 8, nullptr,
-                            nullptr);
+      const int j = (int)(slot % lanes);
+      Ctx &x = j == 0 ? c : c.lanes[j - 1]->c;
+      PassBuffers &bufs = j == 0 ? b.bufs[i] : b.lane_bufs[j - 1][i];
+      DevGraph &g = x.graphs[reqs[i].graph_id];
+      Plan &p = x.plans[reqs[i].query_id];
+      x.cur_tuned_heavy = g.tuned_heavy.count(reqs[i].query_id) ? g.tuned_heavy[reqs[i].query_id] : -1;
+      int rc = enqueue_pass(x, g, p, (int64_t)reqs[i].first_trial + t, bufs, b.results + slot * 8, nullptr, nullptr);
       if (rc != CC_OK) return rc;
     }
+  }
+  for (int j = 0; j < lanes - 1; j++) {
+    Ctx &x = c.lanes[j]->c;
+    c.kernels += x.kernels - k0[j];
+    x.kernels = k0[j];
+    if (cudaEventRecord(b.join[j], x.stream) != cudaSuccess ||
+        cudaStreamWaitEvent(c.stream, b.join[j], 0) != cudaSuccess)
+      return CC_ERR_CUDA;
   }
   return CC_OK;
 }
@@ -124,10 +206,23 @@ extern "C" int cc_count_batch(cc_ctx *ctx, const cc_request *reqs, int n_reqs, u
     b->total = total;
     b->results = (u64 *)dev_alloc(c, total * 8 * sizeof(u64));
     if (!b->results) rc = CC_ERR_OOM;
+    // more lanes than passes would idle
+    const int lanes = std::min<int>(ready_lanes(c, reqs, n_reqs), (int)std::max<size_t>(total, 1));
+    b->lane_bufs.resize(lanes - 1);
+    if (lanes > 1 && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) rc = CC_ERR_CUDA;
+    for (int j = 0; j < lanes - 1 && rc == CC_OK; j++) {
+      b->join.push_back(nullptr);
+      if (cudaEventCreateWithFlags(&b->join.back(), cudaEventDisableTiming) != cudaSuccess) rc = CC_ERR_CUDA;
+    }
     for (int i = 0; i < n_reqs && rc == CC_OK; i++) {
       b->bufs.emplace_back();
       b->graph_of.push_back(reqs[i].graph_id);
       rc = alloc_pass(c, c.graphs[reqs[i].graph_id], c.plans[reqs[i].query_id], b->bufs.back());
+      for (int j = 0; j < lanes - 1 && rc == CC_OK; j++) {
+        Ctx &x = c.lanes[j]->c;
+        b->lane_bufs[j].emplace_back();
+        rc = alloc_pass(x, x.graphs[reqs[i].graph_id], x.plans[reqs[i].query_id], b->lane_bufs[j].back());
+      }
     }
     // eager run: sizes the scratch and gives this call's results
     if (rc == CC_OK) rc = enqueue_batch(c, reqs, n_reqs, *b);
@@ -179,6 +274,13 @@ extern "C" int cc_count_batch(cc_ctx *ctx, const cc_request *reqs, int n_reqs, u
     }
     if (status) status[i] = st;
   }
+  return CC_OK;
+}
+
+extern "C" int cc_set_batch_lanes(cc_ctx *ctx, int lanes) {
+  if (!ctx || lanes < 1 || lanes > 4) return CC_ERR_INVALID_ARG;
+  if (ctx->c.batch_lanes != lanes) batch_cache_clear(ctx->c);
+  ctx->c.batch_lanes = lanes;
   return CC_OK;
 }
 

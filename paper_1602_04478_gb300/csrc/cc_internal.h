@@ -129,6 +129,8 @@ struct Ctx {
   int cur_tuned_heavy = -1;      // tuned threshold of the (graph, query) being enqueued, -1 none
   cudaStream_t own_stream = nullptr;  // created for graph capture when the caller's stream is the legacy one
   bool capture = true;           // batches replay a captured CUDA graph
+  int batch_lanes = 2;           // concurrent lanes of a batch (this context and batch_lanes - 1 others)
+  std::vector<struct cc_ctx *> lanes;  // the other lanes' contexts (own stream and scratch, shared graphs)
   struct BatchCache;
   std::map<std::string, BatchCache *> batches;
   uint64_t kernels = 0;          // kernels launched by this context (a graph replay adds those it holds)

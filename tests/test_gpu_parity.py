@@ -494,13 +494,17 @@ def test_memory_budget_oom(cc):
 
 
 # ------------------------------ batched form ------------------------------
+@pytest.mark.parametrize("lanes", [1, 2, 3])
 @pytest.mark.parametrize("capture", [True, False])
-def test_batch_equals_plain(cc, capture):
+def test_batch_equals_plain(cc, capture, lanes):
+    # the batched form, replayed as a CUDA graph or run eagerly, on one lane
+    # or several concurrent ones: the same counts as one cc_count per colouring
     import paper_1602_04478_gb300 as P
     g1, g2 = graph("cl3000"), graph("er2000")
     a, b = cc.load_graph(g1), cc.load_graph(g2)
     try:
         P.cc_set_graph_capture(cc.h, capture)
+        P.cc_set_batch_lanes(cc.h, lanes)
         P.cc_set_coloring_seed(cc.h, 3)
         qs = {name: cc.set_query(*QUERIES[name]) for name in ["C5", "chord_pendant", "glasses", "C6", "C4"]}
         reqs = [(a, qs["C5"], 0, 4), (a, qs["chord_pendant"], 2, 3), (b, qs["glasses"], 0, 2),
@@ -515,6 +519,7 @@ def test_batch_equals_plain(cc, capture):
         k, e = QUERIES["C5"]
         assert int(res[0][1]) == O.dp_count(g1, k, e, O.colors(3, 1, g1.n, k))[0]
     finally:
+        P.cc_set_batch_lanes(cc.h, 2)
         P.cc_set_graph_capture(cc.h, True)
         cc.free_graph(a)
         cc.free_graph(b)
