@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(256) k_leaf_join_flat(LeafArgs a) {
       const int cy = ok ? a.colors[y] : 0;
       const u64 v = !ok ? 0ull : (a.B.p ? __ldg(a.B.p + (int64_t)y * RB + j) : 1ull);
       const int slot = tx[cy * RB + j];
-      if (v && cc_in(slot, a.RY, a.status)) {
+      // slot -1: the signatures overlap beyond chi(y), no match
+      if (v && slot >= 0 && cc_in(slot, a.RY, a.status)) {
         const unsigned long long old = atomicAdd(Y + slot, v);
         ovf |= (old + v < old);
       }
