@@ -49,10 +49,16 @@ WORKLOAD = {"graph": "chung_lu", "n": 1_000_000, "mean_deg": 16, "gamma": 2.1, "
             "queries": ["C6", "glasses"], "form": "plain", "colourings_per_query_per_step": 1}
 COLOR_SEED = 1
 BATCH_QUERIES = ["C5", "chord_pendant", "glasses"]
-# DRAM bytes (read + written) per colouring of each kernel family, from
-# single-kernel ncu captures of a small case scaled to the full workload by
-# its structural work; None where no capture of the current kernels exists
-TRAFFIC_BYTES = {"cycle_closure": None, "leaf_join": None, "triangle": None}
+# DRAM bytes (read + written) per colouring of each kernel family on the
+# benchmark graph, estimated from an ncu capture of every launch of those
+# kernels on a small case of the same shape (Chung-Lu n = 2e5, mean 16,
+# gamma 2.1; one C6 and one glasses colouring): the small case's DRAM bytes
+# per algorithmic byte times the full workload's algorithmic bytes
+# (closure 24.48 GB / 13.01 GB, leaf joins 0.1325 / 0.978, triangle list
+# 0.204 / 0.963).  The small case's tables fit in L2, so the leaf-join and
+# triangle ratios are lower bounds.
+TRAFFIC_BYTES = {"cycle_closure": 140.90e9 * 24.48 / 13.01, "leaf_join": 4.887e9 * 0.1325 / 0.978,
+                 "triangle": 8.119e9 * 0.204 / 0.963}
 FLUSH_BYTES = 256 << 20
 # CPU baseline: whole colourings on a smaller graph of the benchmark's shape
 CPU_GRAPH = {"graph": "chung_lu", "n": 2_000, "mean_deg": 16, "gamma": 2.1, "seed": 2}
@@ -568,9 +574,12 @@ def run_plan_eval(args):
                     best = ms if best is None else min(best, ms)
                     counts.add(int(col[0]))
                 times.append(best)
-            # the paper's heuristic (its factors alone) and the library's pick
+            # the paper's heuristic (its factors alone), the library's static
+            # pick, and the measured choice (cc_autotune_plan, timed separately)
             h = [i for i, t in enumerate(trees) if t["paper"]][0]
             lib_pick = [i for i, t in enumerate(trees) if t["default"]][0]
+            qa = ctx.set_query(k, e)
+            tuned = P.cc_autotune_plan(ctx.h, gid, qa)
             key = [(t["longest"], t["boundary"], t["annotations"]) for t in trees]
             ties = [i for i in range(len(trees)) if key[i] == key[h]]
             opt = min(range(len(trees)), key=lambda i: times[i])
@@ -578,6 +587,7 @@ def run_plan_eval(args):
                    "heuristic_is_optimal": h == opt, "heuristic_over_optimal": times[h] / times[opt],
                    "library_pick": lib_pick, "library_is_optimal": lib_pick == opt,
                    "library_over_optimal": times[lib_pick] / times[opt],
+                   "measured_pick": tuned, "measured_over_optimal": times[tuned] / times[opt],
                    "trees_tied_with_heuristic": len(ties), "counts_equal": len(counts) == 1,
                    "factors": key, "join_cost": [t["cost"] for t in trees]}
             rows.append(row)
@@ -590,6 +600,8 @@ def run_plan_eval(args):
                       "library_optimal_share": sum(r["library_is_optimal"] for r in rows) / max(1, len(rows)),
                       "library_within_15pct_share": sum(r["library_over_optimal"] <= 1.15 for r in rows) / max(1, len(rows)),
                       "max_library_over_optimal": max((r["library_over_optimal"] for r in rows), default=None),
+                      "measured_within_15pct_share": sum(r["measured_over_optimal"] <= 1.15 for r in rows) / max(1, len(rows)),
+                      "max_measured_over_optimal": max((r["measured_over_optimal"] for r in rows), default=None),
                       "all_counts_equal": all(r["counts_equal"] for r in rows), "per_pair": rows}), flush=True)
     ctx.close()
     return 0
@@ -708,6 +720,8 @@ def main():
         tuned = {name: args.heavy_degree for name in qids}
     else:
         tuned = {name: P.cc_autotune(ctx.h, gid, q) for name, q in qids.items()}
+    # the decomposition tree measured fastest on this graph (queries with one tree keep it)
+    trees = {name: P.cc_autotune_plan(ctx.h, gid, q) for name, q in qids.items()}
     trial_base = rank * 1_000_000
 
     def step(i):
@@ -823,6 +837,8 @@ def main():
         if args.heavy_degree < 0:
             for q in q3.values():
                 P.cc_autotune(ctx.h, gid, q)
+        for q in q3.values():
+            P.cc_autotune_plan(ctx.h, gid, q)
         T3 = args.batch_trials
         first3 = trial_base + 30_000
 
@@ -894,7 +910,7 @@ def main():
                        "units_per_step": units_step, "units_by_query": units},
             "colorings_per_s": colourings, "wall_s": wall, "batched": batched, "batched_config": batch_cfg,
             "config1": config1,
-            "heavy_degree": tuned,
+            "heavy_degree": tuned, "decomposition_tree": trees,
             "kernel_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in kern.items()},
             "gpu_launches": launches, "roofline": roofline, "kernel_rooflines": kernel_rooflines,
             "clocks": clocks, "e2e": e2e,

@@ -229,6 +229,14 @@ int cc_set_batch_lanes(cc_ctx *ctx, int lanes);
  * (nullable) receives the choice. */
 int cc_autotune(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int *heavy_degree);
 
+/* Measured choice of the decomposition tree: every supported tree of
+ * query_id (at most 32, in cc_plan_enumerate's order) counts one colouring
+ * of graph_id after an untimed one; the fastest becomes the query's
+ * decomposition (as cc_set_decomposition would set it, for every graph).
+ * *chosen (nullable) receives its index among the supported trees.  Counts
+ * do not depend on the tree. */
+int cc_autotune_plan(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int *chosen);
+
 /* Serving loop (continuous batching).  A server holds graphs and queries
  * resident on one device and `workers` worker contexts, each with its own
  * CUDA stream and scratch.  Requests (graph, query, trials) are submitted at

@@ -37,7 +37,7 @@ EXPORTED = [
     "cc_set_colors", "cc_clear_colors", "cc_count", "cc_count_per_vertex", "cc_work_units", "cc_work_detail",
     "cc_set_timing",
     "cc_get_timing", "cc_reset_timing", "cc_kernel_launches", "cc_count_cycle_noalloc", "cc_count_batch", "cc_set_graph_capture",
-    "cc_set_batch_lanes",
+    "cc_set_batch_lanes", "cc_autotune_plan",
     "cc_autotune", "cc_server_create", "cc_server_destroy", "cc_server_load_csr", "cc_server_set_query",
     "cc_server_set_coloring_seed", "cc_server_submit", "cc_server_poll", "cc_server_stats", "cc_strerror",
 ]
@@ -111,6 +111,7 @@ def load_library(path: str):
                            ctypes.c_int),
         "cc_set_graph_capture": ([P, ctypes.c_int], ctypes.c_int),
         "cc_set_batch_lanes": ([P, ctypes.c_int], ctypes.c_int),
+        "cc_autotune_plan": ([P, I32, I32, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cc_autotune": ([P, I32, I32, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cc_server_create": ([ctypes.POINTER(P), ctypes.c_int, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
         "cc_server_destroy": ([P], None),
@@ -423,6 +424,14 @@ def cc_set_graph_capture(h, enable: bool) -> None:
 
 def cc_set_batch_lanes(h, lanes: int) -> None:
     _check(lib().cc_set_batch_lanes(h, lanes), "cc_set_batch_lanes")
+
+
+def cc_autotune_plan(h, gid: int, qid: int) -> int:
+    """Time every supported decomposition tree on the graph and keep the
+    fastest; returns its index among the supported trees."""
+    i = ctypes.c_int(0)
+    _check(lib().cc_autotune_plan(h, gid, qid, ctypes.byref(i)), "cc_autotune_plan")
+    return i.value
 
 
 def cc_autotune(h, gid: int, qid: int) -> int:

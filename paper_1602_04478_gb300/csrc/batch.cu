@@ -364,3 +364,65 @@ extern "C" int cc_autotune(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int 
   if (heavy_degree) *heavy_degree = best;
   return CC_OK;
 }
+
+// Measured choice of the decomposition tree (the exhaustive evaluation of
+// Section "Evaluation of Plan Generation Heuristic", run on the caller's
+// graph): every supported tree of the query (at most 32) counts one
+// colouring after an untimed one, timed with CUDA events; the fastest becomes
+// the query's decomposition.  *chosen receives its index among the supported
+// trees in cc_plan_enumerate's order.
+extern "C" int cc_autotune_plan(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int *chosen) {
+  if (!ctx) return CC_ERR_INVALID_ARG;
+  Ctx &c = ctx->c;
+  auto gi = c.graphs.find(graph_id);
+  auto pi = c.plans.find(query_id);
+  if (gi == c.graphs.end() || pi == c.plans.end()) return CC_ERR_INVALID_ARG;
+  DevGraph &g = gi->second;
+  const Plan orig = pi->second;
+  std::vector<PlanChoice> trees;
+  int rc = plan_enumerate(orig.k, orig.edges, trees);
+  if (rc != CC_OK) return rc;
+  std::vector<Plan> plans;
+  for (auto &t : trees) {
+    if (!t.supported || plans.size() >= 32) continue;
+    Plan p;
+    if (plan_explicit(orig.k, orig.edges, t.seq, p) == CC_OK) plans.push_back(p);
+  }
+  if (plans.empty()) return CC_ERR_UNSUPPORTED;
+  cudaSetDevice(c.device);
+  int best = 0;
+  if (plans.size() > 1) {
+    const bool timing = c.timing;
+    c.timing = false;
+    c.cur_tuned_heavy = g.tuned_heavy.count(query_id) ? g.tuned_heavy[query_id] : -1;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best_ms = 0.f;
+    for (size_t i = 0; i < plans.size() && rc == CC_OK; i++) {
+      u64 cnt = 0;
+      bool ovf = false;
+      rc = prepare_plan_graph(c, g, plans[i]);
+      if (rc == CC_OK) rc = run_plan(c, g, plans[i], 1, &cnt, &ovf, nullptr, nullptr);  // untimed
+      cudaEventRecord(a, c.stream);
+      if (rc == CC_OK) rc = run_plan(c, g, plans[i], 0, &cnt, &ovf, nullptr, nullptr);
+      cudaEventRecord(b, c.stream);
+      cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (i == 0 || ms < best_ms) {
+        best_ms = ms;
+        best = (int)i;
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    c.timing = timing;
+    if (rc != CC_OK) return rc;
+  }
+  pi->second = plans[best];
+  for (auto &kv : c.graphs) kv.second.work_detail.erase(query_id);
+  batch_cache_clear(c);
+  if (chosen) *chosen = best;
+  return CC_OK;
+}

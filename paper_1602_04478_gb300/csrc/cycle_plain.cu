@@ -484,49 +484,6 @@ __device__ __forceinline__ void pc_meet(const uint32_t *tag, const PcScratch &S,
   pc_close_x<L>(A, P, act && hit, cu, cx, sA, sP, tid, tot, ovf);
 }
 
-// The meeting vertices of one warp come in a software pipeline: while x_i
-// is visited, the row bounds and colour of x_{i+1} are already in flight, so
-// its tags can be read as soon as its turn comes.
-struct PcRow {
-  int32_t x;
-  int cx;
-  int64_t xb;
-  int deg;
-};
-
-__device__ __forceinline__ PcRow pc_row(const GraphView &g, const uint8_t *colors, int64_t xi, int32_t umax) {
-  PcRow r;
-  r.x = (int32_t)xi;
-  if (xi < umax) {
-    r.cx = colors[r.x];
-    r.xb = g.row[r.x];
-    r.deg = (int)(g.row[r.x + 1] - r.xb);
-  } else {
-    r.cx = 0;
-    r.xb = 0;
-    r.deg = 0;
-  }
-  return r;
-}
-
-__device__ __forceinline__ uint32_t pc_first_tag(const uint32_t *tag, const PcRow &r, int lane) {
-  return lane < r.deg ? __ldg(tag + r.xb + lane) : 0xFFFFFFFFu;
-}
-
-// The first chunk of x from its prefetched tags (membership loaded here).
-// `any` (nullable) receives whether the neighbour is in some source's levels.
-__device__ __forceinline__ PcChunk pc_chunk_from(uint32_t t, const PcScratch &S, const PcRow &r, int lane,
-                                                 int32_t umax, bool *any_out = nullptr) {
-  PcChunk k;
-  k.w = lane < r.deg ? (int32_t)(t & kTagMask) : INT32_MAX;
-  if (k.w < umax && !cc_in(k.w, S.n, S.status)) k.w = INT32_MAX;
-  k.c = k.w < umax ? (int)(t >> kTagShift) : r.cx;
-  const bool any = k.c != r.cx && ((__ldg(S.anym + (k.w >> 5)) >> (k.w & 31)) & 1u);
-  k.m = any ? __ldg(S.member + k.w) : 0ull;
-  if (any_out) *any_out = any;
-  return k;
-}
-
 // One warp per meeting vertex x below the group's highest source, lane b =
 // source b.
 template <int L>
@@ -544,13 +501,13 @@ __global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull(GraphView g, const ui
   unsigned ovf = 0;
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  PcRow r1 = pc_row(g, colors, warp0, umax);
   for (int64_t xi = warp0; xi < umax; xi += nwarps) {
-    const PcRow r = r1;
-    const uint32_t t = pc_first_tag(tag, r, lane);
-    r1 = pc_row(g, colors, xi + nwarps, umax);
-    const PcChunk k = pc_chunk_from(t, S, r, lane, umax);
-    pc_meet<L>(tag, S, r.x, r.cx, r.xb, r.deg, k, lane, active, ub, cu, umax, sA, sP, tid, tot, ovf);
+    const int32_t x = (int32_t)xi;
+    const int cx = colors[x];
+    const int64_t xb = g.row[x];
+    const int deg = (int)(g.row[x + 1] - xb);
+    const PcChunk k = pc_load_chunk(tag, S, xb, deg, lane, cx, umax);
+    pc_meet<L>(tag, S, x, cx, xb, deg, k, lane, active, ub, cu, umax, sA, sP, tid, tot, ovf);
   }
   if (active && tot) atomic_add_ck(S.totals + b, tot, ovf);
   flag_overflow(status, ovf);
@@ -577,18 +534,22 @@ __global__ void __launch_bounds__(kPcThreads, 4) k_pc_pull2(GraphView g, const u
   unsigned ovf = 0;
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  PcRow r1 = pc_row(g, colors, warp0, umax);
   for (int64_t xi = warp0; xi < umax; xi += nwarps) {
-    const PcRow r = r1;
-    const uint32_t t = pc_first_tag(tag, r, lane);
-    r1 = pc_row(g, colors, xi + nwarps, umax);
-    // the map and group A's membership words, then group B's for the same neighbours
-    bool any = false;
-    const PcChunk kA = pc_chunk_from(t, SA, r, lane, umax, &any);
+    const int32_t x = (int32_t)xi;
+    const int cx = colors[x];
+    const int64_t xb = g.row[x];
+    const int deg = (int)(g.row[x + 1] - xb);
+    const uint32_t t = lane < deg ? __ldg(tag + xb + lane) : 0xFFFFFFFFu;
+    PcChunk kA;
+    kA.w = lane < deg ? (int32_t)(t & kTagMask) : INT32_MAX;
+    if (kA.w < umax && !cc_in(kA.w, g.n, status)) kA.w = INT32_MAX;
+    kA.c = kA.w < umax ? (int)(t >> kTagShift) : cx;
+    const bool any = kA.c != cx && ((__ldg(SA.anym + (kA.w >> 5)) >> (kA.w & 31)) & 1u);
+    kA.m = any ? __ldg(SA.member + kA.w) : 0ull;
     PcChunk kB = kA;
     kB.m = any ? __ldg(SB.member + kA.w) : 0ull;
-    pc_meet<L>(tag, SA, r.x, r.cx, r.xb, r.deg, kA, lane, actA, ubA, cuA, umax, sA, sP, tid, totA, ovf);
-    pc_meet<L>(tag, SB, r.x, r.cx, r.xb, r.deg, kB, lane, actB, ubB, cuB, umax, sA, sP, tid, totB, ovf);
+    pc_meet<L>(tag, SA, x, cx, xb, deg, kA, lane, actA, ubA, cuA, umax, sA, sP, tid, totA, ovf);
+    pc_meet<L>(tag, SB, x, cx, xb, deg, kB, lane, actB, ubB, cuB, umax, sA, sP, tid, totB, ovf);
   }
   if (actA && totA) atomic_add_ck(SA.totals + b, totA, ovf);
   if (actB && totB) atomic_add_ck(SB.totals + b, totB, ovf);
