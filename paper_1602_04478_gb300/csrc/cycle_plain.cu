@@ -629,8 +629,11 @@ __global__ void k_pc_finish(PcScratch SA, PcGroup GA, PcScratch SB, PcGroup GB, 
 #ifndef CC_PL_THREADS
 #define CC_PL_THREADS 256
 #endif
-constexpr int kPlThreads = CC_PL_THREADS;      // threads per source (one CTA)
-constexpr int kPlSlotsPerSM = 1024 / kPlThreads;  // resident CTAs per SM, one scratch slot each
+#ifndef CC_PL_SLOTS_PER_SM
+#define CC_PL_SLOTS_PER_SM (1024 / CC_PL_THREADS)
+#endif
+constexpr int kPlThreads = CC_PL_THREADS;          // threads per source (one CTA)
+constexpr int kPlSlotsPerSM = CC_PL_SLOTS_PER_SM;  // resident CTAs per SM, one scratch slot each
 
 __device__ __forceinline__ int pair_idx(int a, int b) {
   int hi = a > b ? a : b, lo = a > b ? b : a;

@@ -173,8 +173,68 @@ __global__ void __launch_bounds__(256) k_leaf_join_flat(LeafArgs a) {
   flag_overflow(a.status, ovf);
 }
 
+// The same join with the lanes on the output slots of Y (Y rows of at most
+// 16 or 32 slots, no A and no edge table): for each neighbour y of x, lane s
+// reads the one entry of y's row whose signature, with chi(x) added, is Y's
+// slot s -- inv[(cx k + cy) RY + s], or -1 when there is none -- and adds it
+// to its own register.  No atomics; a row's entries are read by neighbouring
+// lanes.  With Y rows of at most 16 slots each half-warp takes its own
+// neighbours and the halves are summed at the end.
+__global__ void __launch_bounds__(256) k_leaf_join_slots(LeafArgs a) {
+  extern __shared__ __align__(16) unsigned char slots_smem[];
+  int16_t *inv = reinterpret_cast<int16_t *>(slots_smem);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int k = a.k, RY = a.RY;
+  const int RB = a.B.p ? a.B.R : 1;
+  const int sB = a.B.p ? a.B.s : 1;
+  for (int t = threadIdx.x; t < k * k * RY; t += blockDim.x) inv[t] = -1;
+  __syncthreads();
+  for (int t = threadIdx.x; t < k * k * RB; t += blockDim.x) {
+    const int j = t % RB, cy = (t / RB) % k, cx = t / (RB * k);
+    const uint32_t mB = a.B.p ? umask(a.lut, sB, j, cy) : (1u << cy);
+    if (cx != cy && !(mB >> cx & 1u)) inv[(cx * k + cy) * RY + uslot(a.lut, mB | (1u << cx), cx)] = (int16_t)j;
+  }
+  __syncthreads();
+  const bool halves = RY <= 16;
+  const int s = halves ? (lane & 15) : lane;  // this lane's output slot
+  const int h = halves ? (lane >> 4) : 0;     // which neighbours: h, h + step, ...
+  const int step = halves ? 2 : 1;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned ovf = 0;
+  for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + wib; x < a.g.n; x += nwarps) {
+    const int cx = a.colors[x];
+    const int64_t rb = a.g.row[x];
+    const int deg = (int)(a.g.row[x + 1] - rb);
+    const int16_t *ix = inv + (size_t)cx * k * RY;
+    u64 acc = 0;
+    if (s < RY) {
+      for (int i = h; i < deg; i += step) {
+        const int32_t y = __ldg(a.g.col + rb + i);
+        if (!cc_in(y, a.g.n, a.status)) continue;
+        const int j = ix[a.colors[y] * RY + s];
+        if (j < 0) continue;
+        acc = add_ck(acc, a.B.p ? __ldg(a.B.p + (int64_t)y * RB + j) : 1ull, ovf);
+      }
+    }
+    if (halves) acc = add_ck(acc, __shfl_down_sync(0xffffffffu, acc, 16), ovf);
+    if (lane < RY) a.out[x * (int64_t)a.R_out + lane] = acc;
+  }
+  flag_overflow(a.status, ovf);
+}
+
 int launch_leaf(Ctx &c, const LeafArgs &a) {
   const int RB = a.B.p ? a.B.R : 1;
+  if (!a.E.p && !a.A.p && a.RY <= 32 && a.RY == a.R_out && a.k * a.k * (a.RY + RB) <= kFlatMaxTable) {
+    const size_t smem = (size_t)a.k * a.k * a.RY * sizeof(int16_t);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_leaf_join_slots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int64_t blocks = std::min<int64_t>(std::max<int64_t>((a.g.n + 7) / 8, 1), 152 * 8);
+    timing_begin(c, "leaf_join");
+    k_leaf_join_slots<<<(unsigned)blocks, 256, smem, c.stream>>>(a);
+    c.kernels++;
+    timing_end(c);
+    return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
+  }
   if (!a.E.p && a.k * a.k * RB <= kFlatMaxTable) {
     const size_t smem = (size_t)8 * a.RY * sizeof(u64) + (size_t)a.k * a.k * RB * sizeof(int16_t);
     if (smem > 200 * 1024) return CC_ERR_UNSUPPORTED;
