@@ -124,8 +124,10 @@ int cc_graph_info(cc_ctx *ctx, int32_t graph_id, int64_t *n, int64_t *nnz, int64
  * edges and induced cycles with at most two boundary nodes, contracted by
  * Cases 1-3) and computes aut(Q) by enumeration.  CC_ERR_NOT_TW2 when no
  * decomposition exists (Lemma 4.1), CC_ERR_UNSUPPORTED when every
- * decomposition needs a non-root cycle block longer than a triangle or a
- * root cycle longer than 8. */
+ * decomposition needs a non-root cycle block longer than a triangle with two
+ * boundary nodes (Case 2), or a cycle longer than 8.  Non-root cycles of
+ * length >= 4 with one boundary node (Case 1) are built from the general
+ * per-source kernel rooted at the boundary node (no vertex order). */
 int cc_set_query(cc_ctx *ctx, int k, int n_edges, const int32_t *edges, int32_t *query_id);
 
 /* Replace the query's decomposition by an explicit contraction order.
@@ -146,8 +148,8 @@ int cc_set_decomposition(cc_ctx *ctx, int32_t query_id, const int32_t *block_seq
  * number of boundary nodes, the boundary nodes, the number of children, the
  * children's block indices -- into out[cap] and aut(Q) into *aut.  Returns the
  * number of int32 words (more than cap means truncated) or a CC_ERR_ code.
- * A plan with a kind-4 block is returned too; cc_set_query refuses it with
- * CC_ERR_UNSUPPORTED. */
+ * A plan whose kind-4 block has two boundary nodes is returned too;
+ * cc_set_query refuses it with CC_ERR_UNSUPPORTED. */
 int cc_plan_inspect(int k, int n_edges, const int32_t *edges, const int32_t *block_seq, int seq_len,
                     int32_t *out, int cap, int64_t *aut);
 

@@ -254,7 +254,8 @@ def cc_plan_inspect(k: int, edges, block_seq=None, allow_unsupported: bool = Fal
     """Decomposition the library uses (host only).  Returns (blocks, aut).
 
     Raises CCError(CC_ERR_UNSUPPORTED) when a block has no kernel (a non-root
-    cycle longer than a triangle) unless allow_unsupported."""
+    cycle longer than a triangle with two boundary nodes) unless
+    allow_unsupported."""
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
     s = np.ascontiguousarray(np.asarray(block_seq if block_seq else [0], dtype=np.int32).reshape(-1))
     out = np.zeros(4096, dtype=np.int32)
@@ -265,7 +266,8 @@ def cc_plan_inspect(k: int, edges, block_seq=None, allow_unsupported: bool = Fal
     if w < 0:
         raise CCError(w, "cc_plan_inspect")
     blocks = decode_plan_records(out, w)
-    if not allow_unsupported and any(b["kind"] == "cycle" or (b["kind"] == "root_cycle" and len(b["nodes"]) > 8)
+    if not allow_unsupported and any((b["kind"] == "cycle" and (len(b["boundary"]) != 1 or len(b["nodes"]) > 8))
+                                     or (b["kind"] == "root_cycle" and len(b["nodes"]) > 8)
                                      for b in blocks):
         raise CCError(-9, "cc_plan_inspect")
     return blocks, aut.value

@@ -135,7 +135,7 @@ TabE tab_e(const std::vector<Table> &T, int idx, bool use_rev) {
 
 size_t table_bytes(const Plan &p, const Stage &st, const DevGraph &g, int *R_out, int *arity) {
   int k = p.k;
-  if (st.kind == ST_LEAF || (st.kind == ST_TRI && st.nb == 1)) {
+  if (st.kind == ST_LEAF || (st.kind == ST_TRI && st.nb == 1) || (st.kind == ST_CYCLE_NONROOT && st.nb == 1)) {
     *arity = 1;
     *R_out = (int)binom(k - 1, st.s - 1);
     return (size_t)g.n * *R_out * 8;
@@ -325,6 +325,39 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
       a.count_units = count_units;
       rc = launch_cycle(c, a);
       if (rc != CC_OK) c.scratch_dirty = c.hv_dirty = true;
+    } else if (st.kind == ST_CYCLE_NONROOT && st.nb == 1) {
+      // Case 1 block, L >= 4: its unary table by the image of the boundary
+      // node, from the general kernel rooted there -- the cycle rotated so
+      // the boundary node is a_0, one split at a_0 and its opposite node,
+      // no vertex order (the image of a_0 is fixed, not the highest)
+      const int L = st.L;
+      int p0 = 0;
+      while (p0 < L && st.nodes[p0] != st.bd[0]) p0++;
+      if (p0 == L) { rc = CC_ERR_INVALID_ARG; break; }
+      CycleArgs a;
+      a.g = gv;
+      a.colors = B.colors;
+      a.k = k;
+      a.lut = lut;
+      a.L = L;
+      for (int j = 0; j < L; j++) {
+        const int o = (j + p0) % L;
+        a.N[j] = tab_u(T, st.node_child[o]);
+        a.Efw[j] = tab_e(T, st.edge_child[o], !st.edge_fwd[o]);
+        a.Ebw[j] = tab_e(T, st.edge_child[o], st.edge_fwd[o]);
+      }
+      a.no_order = true;
+      a.n_h = 1;
+      a.hs[0] = 0;
+      a.multiplier = 1;
+      a.per_vertex = nullptr;
+      a.status = status;
+      a.count_units = count_units;
+      a.out = T[i].p;
+      a.R_out = R;
+      a.s_out = st.s;
+      rc = launch_cycle(c, a);
+      if (rc != CC_OK) c.scratch_dirty = c.hv_dirty = true;
     } else if (st.kind == ST_ROOT_NODE) {
       const Table &ct = T[st.node_child[0]];
       if (ct.R != 1) { rc = CC_ERR_INVALID_ARG; break; }
@@ -342,7 +375,7 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
       const double dev_units = (double)(now[ST_UNITS] - seen[ST_UNITS]);
       w.units += dev_units;
       if (st.kind == ST_TRI) w.bytes += 4.0 * dev_units;
-      if (st.kind == ST_CYCLE_ROOT) {
+      if (st.kind == ST_CYCLE_ROOT || st.kind == ST_CYCLE_NONROOT) {
         for (int j = 0; j < 8; j++) {
           w.scans[j] = (double)(now[ST_SCAN0 + j] - seen[ST_SCAN0 + j]);
           w.bytes += 4.0 * w.scans[j];  // one neighbour id per scanned edge
@@ -402,7 +435,7 @@ const char *cc_strerror(int code) {
     case CC_ERR_OVERFLOW: return "a count exceeded 2^64-1";
     case CC_ERR_TIMEOUT: return "a bounded device wait gave up";
     case CC_ERR_CUDA: return "CUDA runtime error";
-    case CC_ERR_UNSUPPORTED: return "query needs a block kind without a kernel (non-root cycle longer than 3, or root cycle longer than 8)";
+    case CC_ERR_UNSUPPORTED: return "query needs a block kind without a kernel (non-root cycle longer than 3 with two boundary nodes, or a cycle longer than 8)";
     case CC_ERR_NOT_CONNECTED: return "query graph is not connected";
     case CC_ERR_BOUNDS: return "an index left its array (bounds-check build)";
     default: return "unknown error";

@@ -15,7 +15,7 @@ constexpr int kMaxK = CC_MAX_K;
 constexpr int kMaxCycle = 8;  // longest root cycle the closure kernel handles
 
 // ------------------------------- query plan -------------------------------
-enum StageKind { ST_LEAF = 0, ST_TRI = 1, ST_CYCLE_ROOT = 2, ST_ROOT_NODE = 3 };
+enum StageKind { ST_LEAF = 0, ST_TRI = 1, ST_CYCLE_ROOT = 2, ST_ROOT_NODE = 3, ST_CYCLE_NONROOT = 4 };
 
 // One block of the decomposition tree (Section 4.1) in contraction order.
 struct Stage {

@@ -94,6 +94,11 @@ struct CycleArgs {
   bool count_units = false;   // add the structural edge-subset work to status[ST_UNITS]
   int32_t light_end = 0;      // the per-CTA kernel takes sources of rank < light_end
   bool no_order = false;      // PS procedure: paths from u are not restricted to vertices below u
+  // non-root cycle with one boundary node at position 0 (no_order): the
+  // unary table [n][R_out] over signatures of size s_out, by the image u of
+  // the boundary node, instead of a count
+  u64 *out = nullptr;
+  int R_out = 0, s_out = 0;
 };
 int run_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank, int B);
 bool plain_cycle_eligible(const CycleArgs &a);

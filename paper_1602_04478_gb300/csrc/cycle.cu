@@ -215,6 +215,9 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
   SlotPtrs P = slot_ptrs(sc, blockIdx.x);
   u64 *accP = smem_acc + (size_t)wib * 2 * sc.acc_stride;
   u64 *accM = accP + sc.acc_stride;
+  // unary output (non-root cycle): the current source's row, gathered here
+  unsigned long long *orow = smem_acc + (size_t)kWarps * 2 * sc.acc_stride;
+  for (int i = tid; i < (a.out ? a.R_out : 0); i += kCtaThreads) orow[i] = 0;
   unsigned ovf = 0;
   const int rp = L / 2, rm = L - L / 2;
   while (true) {
@@ -454,6 +457,23 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
                   uint32_t mn = nrow ? umask(a.lut, lp_last.N.s, l, cx) : (1u << cx);
                   if ((mp & mn) != (1u << cx)) continue;
                   uint32_t m1 = mp | mn;
+                  if (a.out) {
+                    // non-root block: every P- signature meeting m1 in {chi(u), chi(x)};
+                    // the union is the block's signature, counted at u's row
+                    const u64 vpn = mul_ck(vp, vn, ovf);
+                    for (int t2 = 0; t2 < RM; t2++) {
+                      const u64 vm = accM[t2];
+                      if (!vm) continue;
+                      const uint32_t mm = pmask(a.lut, lm_last.s_pre, t2, cu, cx);
+                      if ((m1 & mm) != ((1u << cu) | (1u << cx))) continue;
+                      const u64 v = mul_ck(vpn, vm, ovf);
+                      const int slot = uslot(a.lut, m1 | mm, cu);
+                      if (!cc_in(slot, a.R_out, a.status)) continue;
+                      const unsigned long long old = atomicAdd(orow + slot, v);
+                      ovf |= (old + v < old);
+                    }
+                    continue;
+                  }
                   uint32_t m2 = (K & ~m1) | (1u << cu) | (1u << cx);
                   u64 vm = accM[pslot(a.lut, m2, cu, cx)];
                   if (!vm) continue;
@@ -492,6 +512,13 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
           P.xlist[i] = 0;
         }
         __syncthreads();
+      }
+      if (a.out) {
+        // u's row of the non-root block's table (only this CTA writes it)
+        for (int i = tid; i < a.R_out; i += kCtaThreads) {
+          a.out[(int64_t)u * a.R_out + i] = orow[i];
+          orow[i] = 0;
+        }
       }
     }
     if (ovf) atomicOr(&s_ovf, 1u);
@@ -616,7 +643,7 @@ int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   }
   if (cudaMemsetAsync(counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
   sc.epoch = 0;
-  size_t smem = (size_t)kWarps * 2 * sc.acc_stride * sizeof(u64);
+  size_t smem = (size_t)kWarps * 2 * sc.acc_stride * sizeof(u64) + (a.out ? (size_t)a.R_out * sizeof(u64) : 0);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   timing_begin(c, "cycle_closure");
   k_cycle<<<slots, kCtaThreads, smem, c.stream>>>(a, sc, counter);

@@ -29,7 +29,6 @@
 namespace cc {
 namespace {
 
-enum { ST_CYCLE_NONROOT = 4 };
 
 struct QS {
   int k = 0;
@@ -243,13 +242,15 @@ bool try_root(QS &s, std::vector<Stage> &st, bool *ok) {
 // library inserts one engine-aware factor after the longest cycle (see
 // join_cost) unless `paper_only`.
 struct Score {
-  int unsupported, longest;
+  int unsupported, longest, nonroot_long;
   double cost;
   int boundary, annotations, stages;
   bool paper_only;
   bool operator<(const Score &o) const {
     if (unsupported != o.unsupported) return unsupported < o.unsupported;
     if (longest != o.longest) return longest < o.longest;
+    // non-root cycles of length >= 4 run on the general per-source kernel
+    if (!paper_only && nonroot_long != o.nonroot_long) return nonroot_long < o.nonroot_long;
     if (!paper_only && cost != o.cost) return cost < o.cost;
     if (boundary != o.boundary) return boundary < o.boundary;
     if (annotations != o.annotations) return annotations < o.annotations;
@@ -294,9 +295,11 @@ double join_cost(const std::vector<Stage> &st, int k) {
 }
 
 Score score_of(const std::vector<Stage> &st, int k = 0, bool paper_only = false) {
-  Score sc{0, 0, 0.0, 0, 0, (int)st.size(), paper_only};
+  Score sc{0, 0, 0, 0.0, 0, 0, (int)st.size(), paper_only};
   for (auto &g : st) {
-    if (g.kind == ST_CYCLE_NONROOT) sc.unsupported = 1;
+    // non-root cycles of length >= 4: one boundary node (Case 1) only
+    if (g.kind == ST_CYCLE_NONROOT && (g.nb != 1 || g.L > kMaxCycle)) sc.unsupported = 1;
+    if (g.kind == ST_CYCLE_NONROOT) sc.nonroot_long++;
     if (g.kind == ST_CYCLE_ROOT && g.L > kMaxCycle) sc.unsupported = 1;
     if (g.kind == ST_TRI || g.kind == ST_CYCLE_ROOT || g.kind == ST_CYCLE_NONROOT)
       sc.longest = std::max(sc.longest, g.L);

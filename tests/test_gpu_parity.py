@@ -436,11 +436,12 @@ def test_k_range_error(cc):
 
 
 def test_unsupported_block_reported(cc):
-    # two 4-cycles sharing a node: one must be a non-root 4-cycle block
+    # K_{2,3}: every 4-cycle block has two boundary nodes that are not
+    # adjacent (Case 2 with a non-adjacent pair), which has no kernel
     import paper_1602_04478_gb300 as P
-    e = [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (4, 5), (5, 6), (6, 0)]
+    e = [(0, 2), (2, 1), (1, 3), (3, 0), (0, 4), (4, 1)]
     with pytest.raises(P.CCError) as ei:
-        cc.set_query(7, e)
+        cc.set_query(5, e)
     assert P.ERRORS[ei.value.code] == "CC_ERR_UNSUPPORTED"
 
 
