@@ -6,6 +6,8 @@
 // from its children's tables, and the root block is reduced to the count of
 // colourful matches.  Tables of a block are freed once its parent has run.
 // The estimate is colorful * k^k / k! / aut(Q) (Section 2).
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -83,7 +85,10 @@ int ensure_tag_scratch(Ctx &c, size_t bytes) {
   return c.tag_scratch ? CC_OK : CC_ERR_OOM;
 }
 
+// Every timed stage is also an NVTX range (header-only NVTX 3; a no-op
+// unless a profiler listens), whether or not event timing is on.
 void timing_begin(Ctx &c, const char *name) {
+  nvtxRangePushA(name);
   if (!c.timing) return;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
@@ -93,6 +98,7 @@ void timing_begin(Ctx &c, const char *name) {
 }
 
 void timing_end(Ctx &c) {
+  nvtxRangePop();
   if (!c.timing || c.pending.empty()) return;
   cudaEventRecord(c.pending.back().second.second, c.stream);
 }

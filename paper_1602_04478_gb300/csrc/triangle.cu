@@ -796,21 +796,28 @@ int launch_triangle_form(Ctx &c, const TriArgs &a, const TriMode &md, const char
       return CC_ERR_CUDA;
     grid = std::min<int64_t>((int64_t)std::max(per_sm, 1) * sms, n - u_lo);
   }
+  int rc = CC_OK;
   timing_begin(c, name);
   if (u_lo < n) {
-    if (cudaMemsetAsync(a.work_counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
-    k_triangle_hub<kForm><<<(int)grid, kHubThreads, smem, c.stream>>>(a, md, u_lo, max_slots, R_acc);
-    c.kernels++;
-    if (cudaGetLastError() != cudaSuccess) return CC_ERR_CUDA;
+    if (cudaMemsetAsync(a.work_counter, 0, sizeof(int), c.stream) != cudaSuccess) {
+      rc = CC_ERR_CUDA;
+    } else {
+      k_triangle_hub<kForm><<<(int)grid, kHubThreads, smem, c.stream>>>(a, md, u_lo, max_slots, R_acc);
+      c.kernels++;
+      if (cudaGetLastError() != cudaSuccess) rc = CC_ERR_CUDA;
+    }
   }
-  if (u_lo > 0) {
-    if (cudaMemsetAsync(a.work_counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
-    k_triangle<kForm><<<152 * 8, 256, 0, c.stream>>>(a, md, u_lo);
-    c.kernels++;
-    if (cudaGetLastError() != cudaSuccess) return CC_ERR_CUDA;
+  if (rc == CC_OK && u_lo > 0) {
+    if (cudaMemsetAsync(a.work_counter, 0, sizeof(int), c.stream) != cudaSuccess) {
+      rc = CC_ERR_CUDA;
+    } else {
+      k_triangle<kForm><<<152 * 8, 256, 0, c.stream>>>(a, md, u_lo);
+      c.kernels++;
+      if (cudaGetLastError() != cudaSuccess) rc = CC_ERR_CUDA;
+    }
   }
   timing_end(c);
-  return CC_OK;
+  return rc;
 }
 
 int launch_triangle(Ctx &c, const TriArgs &a_in) {
