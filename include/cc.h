@@ -148,10 +148,19 @@ int cc_set_decomposition(cc_ctx *ctx, int32_t query_id, const int32_t *block_seq
  * number of boundary nodes, the boundary nodes, the number of children, the
  * children's block indices -- into out[cap] and aut(Q) into *aut.  Returns the
  * number of int32 words (more than cap means truncated) or a CC_ERR_ code.
- * A plan whose kind-4 block has two boundary nodes is returned too;
- * cc_set_query refuses it with CC_ERR_UNSUPPORTED. */
+ * A plan the kernels cannot run is returned too (cc_plan_supported tells). */
 int cc_plan_inspect(int k, int n_edges, const int32_t *edges, const int32_t *block_seq, int seq_len,
                     int32_t *out, int cap, int64_t *aut);
+
+/* Host-only: 1 if the kernels run the plan cc_plan_inspect describes for the
+ * same arguments, 0 if not (cc_set_query / cc_set_decomposition would answer
+ * CC_ERR_UNSUPPORTED), or a CC_ERR_ code for an invalid query or order.  Not
+ * run: a cycle longer than 8; a triangle or leaf block that reads, or a
+ * triangle that writes, a Case-2 table keyed by pairs that need not be data
+ * edges (Section 4.1, Case 2: boundary nodes not adjacent in their cycle);
+ * a cycle reading more than four such tables; a Case-2 cycle whose longer
+ * side between its boundary nodes has more than 5 edges. */
+int cc_plan_supported(int k, int n_edges, const int32_t *edges, const int32_t *block_seq, int seq_len);
 
 /* Host-only: every decomposition tree of a query (Section 5.3), one record
  * per distinct tree -- sequence length m, supported (1 when the library has

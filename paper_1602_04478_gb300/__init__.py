@@ -32,7 +32,8 @@ EXPORTED = [
     "cc_create", "cc_destroy", "cc_set_allocator", "cc_set_memory_budget", "cc_set_heavy_degree",
     "cc_set_procedure", "cc_set_triangle_list",
     "cc_load_csr", "cc_free_graph",
-    "cc_graph_info", "cc_set_query", "cc_set_decomposition", "cc_plan_inspect", "cc_plan_enumerate", "cc_query_info",
+    "cc_graph_info", "cc_set_query", "cc_set_decomposition", "cc_plan_inspect", "cc_plan_supported", "cc_plan_enumerate",
+    "cc_query_info",
     "cc_set_coloring_seed",
     "cc_set_colors", "cc_clear_colors", "cc_count", "cc_count_per_vertex", "cc_work_units", "cc_work_detail",
     "cc_set_timing",
@@ -91,6 +92,7 @@ def load_library(path: str):
         "cc_set_decomposition": ([P, I32, I32P, ctypes.c_int], ctypes.c_int),
         "cc_plan_inspect": ([ctypes.c_int, ctypes.c_int, I32P, I32P, ctypes.c_int, I32P, ctypes.c_int, I64P],
                             ctypes.c_int),
+        "cc_plan_supported": ([ctypes.c_int, ctypes.c_int, I32P, I32P, ctypes.c_int], ctypes.c_int),
         "cc_plan_enumerate": ([ctypes.c_int, ctypes.c_int, I32P, I32P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
                               ctypes.c_int),
         "cc_query_info": ([P, I32, ctypes.POINTER(ctypes.c_int), I64P, ctypes.POINTER(ctypes.c_int),
@@ -253,9 +255,8 @@ def decode_plan_records(out, w=None):
 def cc_plan_inspect(k: int, edges, block_seq=None, allow_unsupported: bool = False):
     """Decomposition the library uses (host only).  Returns (blocks, aut).
 
-    Raises CCError(CC_ERR_UNSUPPORTED) when a block has no kernel (a non-root
-    cycle longer than a triangle with two boundary nodes) unless
-    allow_unsupported."""
+    Raises CCError(CC_ERR_UNSUPPORTED) when the kernels cannot run the plan
+    (cc_plan_supported) unless allow_unsupported."""
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
     s = np.ascontiguousarray(np.asarray(block_seq if block_seq else [0], dtype=np.int32).reshape(-1))
     out = np.zeros(4096, dtype=np.int32)
@@ -266,11 +267,20 @@ def cc_plan_inspect(k: int, edges, block_seq=None, allow_unsupported: bool = Fal
     if w < 0:
         raise CCError(w, "cc_plan_inspect")
     blocks = decode_plan_records(out, w)
-    if not allow_unsupported and any((b["kind"] == "cycle" and (len(b["boundary"]) != 1 or len(b["nodes"]) > 8))
-                                     or (b["kind"] == "root_cycle" and len(b["nodes"]) > 8)
-                                     for b in blocks):
+    if not allow_unsupported and cc_plan_supported(k, edges, block_seq) == 0:
         raise CCError(-9, "cc_plan_inspect")
     return blocks, aut.value
+
+
+def cc_plan_supported(k: int, edges, block_seq=None) -> int:
+    """1 if the kernels run the plan (host only), else 0."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    s = np.ascontiguousarray(np.asarray(block_seq if block_seq else [0], dtype=np.int32).reshape(-1))
+    rc = lib().cc_plan_supported(k, int(e.shape[0]), _ptr(e, ctypes.c_int32), _ptr(s, ctypes.c_int32),
+                                 len(block_seq) if block_seq else 0)
+    if rc < 0:
+        raise CCError(rc, "cc_plan_supported")
+    return rc
 
 
 def cc_plan_enumerate(k: int, edges):

@@ -21,7 +21,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libcc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-SOURCES = ["api.cu", "graph.cu", "join.cu", "triangle.cu", "cycle.cu", "cycle_heavy.cu", "cycle_plain.cu", "noalloc.cu", "batch.cu", "serve.cu", "plan.cpp"]
+SOURCES = ["api.cu", "graph.cu", "join.cu", "triangle.cu", "cycle.cu", "cycle_heavy.cu", "cycle_plain.cu", "noalloc.cu", "batch.cu", "serve.cu", "pair.cu", "plan.cpp"]
 # name -> (translation units that read the switch, extra flags)
 VARIANTS = {
     # the per-CTA push's bounded wait gives up on its first entry

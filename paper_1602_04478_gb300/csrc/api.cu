@@ -129,14 +129,57 @@ TabU tab_u(const std::vector<Table> &T, int idx) {
   t.R = T[idx].R;
   return t;
 }
+// A pair-keyed table comes back with gi = its stage index; bind_pairs then
+// gives it a slot of the cycle's pair graphs (other kernels refuse it).
 TabE tab_e(const std::vector<Table> &T, int idx, bool use_rev) {
   TabE t;
   if (idx < 0) return t;
-  t.p = T[idx].p;
+  t.p = T[idx].pair ? T[idx].pg.rows : T[idx].p;
   t.s = T[idx].s;
   t.R = T[idx].R;
   t.use_rev = use_rev;
+  if (T[idx].pair) {
+    t.gi = idx;
+    t.ridx = T[idx].pg.ridx;
+  }
   return t;
+}
+
+GraphView pair_view(const PairGraph &pg) {
+  GraphView v;
+  v.n = pg.n;
+  v.nnz = pg.nnz;
+  v.row = pg.row;
+  v.col = pg.col;
+  v.rev = pg.rev;
+  v.lo_cnt = pg.lo_cnt;
+  return v;
+}
+
+// Stage indices in the cycle's edge tables -> slots of a.pg.
+int bind_pairs(CycleArgs &a, const std::vector<Table> &T) {
+  int used[kMaxPairGraphs], n_used = 0;
+  for (int i = 0; i < a.L; i++)
+    for (TabE *E : {&a.Efw[i], &a.Ebw[i]}) {
+      if (E->gi < 0) continue;
+      int slot = -1;
+      for (int j = 0; j < n_used; j++)
+        if (used[j] == E->gi) slot = j;
+      if (slot < 0) {
+        if (n_used == kMaxPairGraphs) return CC_ERR_UNSUPPORTED;
+        slot = n_used;
+        used[n_used++] = E->gi;
+        a.pg[slot] = pair_view(T[E->gi].pg);
+      }
+      E->gi = slot;
+    }
+  return CC_OK;
+}
+
+bool any_pair(const TabE *E, int n) {
+  for (int i = 0; i < n; i++)
+    if (E[i].gi >= 0) return true;
+  return false;
 }
 
 size_t table_bytes(const Plan &p, const Stage &st, const DevGraph &g, int *R_out, int *arity) {
@@ -146,10 +189,11 @@ size_t table_bytes(const Plan &p, const Stage &st, const DevGraph &g, int *R_out
     *R_out = (int)binom(k - 1, st.s - 1);
     return (size_t)g.n * *R_out * 8;
   }
-  if (st.kind == ST_TRI && st.nb == 2) {
+  if ((st.kind == ST_TRI || st.kind == ST_CYCLE_NONROOT) && st.nb == 2) {
     *arity = 2;
     *R_out = (int)binom(k - 2, st.s - 2);
-    return (size_t)std::max<int64_t>(g.nnz, 1) * *R_out * 8;
+    // a pair-keyed table is sized by its count pass during the pass
+    return st.pair_out ? 0 : (size_t)std::max<int64_t>(g.nnz, 1) * *R_out * 8;
   }
   *arity = 0;
   *R_out = 0;
@@ -185,6 +229,9 @@ int alloc_pass(Ctx &c, const DevGraph &g, const Plan &p, PassBuffers &B) {
   for (size_t i = 0; i < p.stages.size(); i++) {
     int R = 0, ar = 0;
     size_t bytes = table_bytes(p, p.stages[i], g, &R, &ar);
+    B.T[i].arity = ar;
+    B.T[i].s = p.stages[i].s;
+    B.T[i].R = R;
     if (!bytes) continue;
     B.T[i].p = (u64 *)dev_alloc(c, bytes);
     if (!B.T[i].p) return CC_ERR_OOM;
@@ -197,12 +244,116 @@ int alloc_pass(Ctx &c, const DevGraph &g, const Plan &p, PassBuffers &B) {
 }
 
 void free_pass(Ctx &c, const DevGraph &g, PassBuffers &B) {
-  for (auto &t : B.T) dev_free(c, t.p, t.bytes);
+  for (auto &t : B.T) {
+    dev_free(c, t.p, t.bytes);
+    if (t.pair) pair_graph_free(c, t.pg);
+  }
   B.T.clear();
   dev_free(c, B.colors, (size_t)g.n);
   dev_free(c, B.counter, 256);
   B.colors = nullptr;
   B.counter = nullptr;
+}
+
+// Case-2 block of length L >= 4 (two boundary nodes b0 = bd[0], b1 =
+// bd[1]): its table cnt(u, x, alpha | B) with u the image of b0 and x that of
+// b1, from the general kernel rooted at b0.  The cycle is rotated (and
+// reflected if that brings b1 nearer) so that b0 is a_0 and b1 is a_p with
+// p <= L/2, and cut at a_0 and a_p: P+ = a_0 .. a_p, P- = a_0, a_{L-1} .. a_p,
+// joined at x (Procedure 2 with the cut at the two boundary nodes, no vertex
+// order).  A boundary pair joined by a data edge (p = 1) fills the
+// edge-keyed table at pos(u -> x); any other pair goes to a pair list --
+// counted by one launch, appended by a second into buffers of that size --
+// and then into the pair graph a parent walks.  Synchronises (pair lists).
+int run_case2(Ctx &c, DevGraph &g, const GraphView &gv, const Lut &lut, const uint8_t *colors, int k,
+              const Stage &st, std::vector<Table> &T, size_t i, u64 *status, bool count_units) {
+  const int L = st.L;
+  int p0 = -1, q0 = -1;
+  for (int j = 0; j < L; j++) {
+    if (st.nodes[j] == st.bd[0]) p0 = j;
+    if (st.nodes[j] == st.bd[1]) q0 = j;
+  }
+  if (p0 < 0 || q0 < 0) return CC_ERR_INVALID_ARG;
+  const int d = (q0 - p0 + L) % L;
+  const bool reflect = d > L / 2;
+  CycleArgs a;
+  a.g = gv;
+  a.colors = colors;
+  a.k = k;
+  a.lut = lut;
+  a.L = L;
+  for (int j = 0; j < L; j++) {
+    if (!reflect) {
+      const int o = (j + p0) % L;  // node j is nodes[o]; edge j joins nodes[o] -> nodes[o+1]
+      a.N[j] = tab_u(T, st.node_child[o]);
+      a.Efw[j] = tab_e(T, st.edge_child[o], !st.edge_fwd[o]);
+      a.Ebw[j] = tab_e(T, st.edge_child[o], st.edge_fwd[o]);
+    } else {
+      const int o = (p0 - j + L) % L;           // node j is nodes[o]
+      const int eo = (p0 - j - 1 + 2 * L) % L;  // edge j joins nodes[o] -> nodes[o-1]: edge eo backwards
+      a.N[j] = tab_u(T, st.node_child[o]);
+      a.Efw[j] = tab_e(T, st.edge_child[eo], st.edge_fwd[eo]);
+      a.Ebw[j] = tab_e(T, st.edge_child[eo], !st.edge_fwd[eo]);
+    }
+  }
+  a.split = reflect ? L - d : d;
+  a.no_order = true;
+  a.n_h = 1;
+  a.hs[0] = 0;
+  a.multiplier = 1;
+  a.per_vertex = nullptr;
+  a.status = status;
+  a.count_units = count_units;
+  a.R_out = T[i].R;
+  a.s_out = st.s;
+  int rc = bind_pairs(a, T);
+  if (rc != CC_OK) return rc;
+  if (!st.pair_out) {
+    // the boundary pair is the cycle edge a_0 a_1 and a data edge
+    if (a.split != 1 || a.Efw[0].gi >= 0 || !T[i].p) return CC_ERR_INVALID_ARG;
+    a.out_mode = 2;
+    a.out = T[i].p;
+    rc = launch_cycle(c, a);
+    if (rc != CC_OK) c.scratch_dirty = c.hv_dirty = true;
+    return rc;
+  }
+  // pair list: count, size, append, then the pair graph
+  if (T[i].pair) pair_graph_free(c, T[i].pg);
+  T[i].pair = false;
+  unsigned long long *cnt = (unsigned long long *)dev_alloc(c, 16);
+  if (!cnt) return CC_ERR_OOM;
+  unsigned long long *keys = nullptr;
+  u64 *rows = nullptr;
+  unsigned long long np = 0;
+  const size_t R = (size_t)T[i].R;
+  do {
+    a.out_mode = 3;
+    a.pair_count = cnt;
+    if ((rc = check(cudaMemsetAsync(cnt, 0, 16, c.stream))) != CC_OK) break;
+    if ((rc = launch_cycle(c, a)) != CC_OK) break;
+    if ((rc = check(cudaMemcpyAsync(&np, cnt, 8, cudaMemcpyDeviceToHost, c.stream))) != CC_OK) break;
+    if ((rc = check(cudaStreamSynchronize(c.stream))) != CC_OK) break;
+    keys = (unsigned long long *)dev_alloc(c, (size_t)std::max<unsigned long long>(np, 1) * 8);
+    rows = (u64 *)dev_alloc(c, (size_t)std::max<unsigned long long>(np, 1) * R * 8);
+    if (!keys || !rows) { rc = CC_ERR_OOM; break; }
+    a.pair_keys = keys;
+    a.pair_rows = rows;
+    a.pair_cap = (int64_t)np;
+    a.count_units = false;  // the structural work was counted by the first launch
+    if ((rc = check(cudaMemsetAsync(cnt, 0, 16, c.stream))) != CC_OK) break;
+    if ((rc = launch_cycle(c, a)) != CC_OK) break;
+    T[i].pg.rows = rows;
+    T[i].pg.R = (int)R;
+    T[i].pair = true;
+    rows = nullptr;  // owned by the pair graph now
+    rc = pair_graph_build(c, g.n, keys, (int64_t)np, T[i].pg);
+  } while (false);
+  if (rc != CC_OK) c.scratch_dirty = c.hv_dirty = true;
+  cudaStreamSynchronize(c.stream);
+  dev_free(c, cnt, 16);
+  dev_free(c, keys, (size_t)std::max<unsigned long long>(np, 1) * 8);
+  dev_free(c, rows, (size_t)std::max<unsigned long long>(np, 1) * R * 8);
+  return rc;
 }
 
 // Issue one colouring pass of the plan on the context's stream: status words
@@ -241,6 +392,7 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
       a.A = tab_u(T, st.node_child[0]);
       a.B = tab_u(T, st.node_child[1]);
       a.E = tab_e(T, st.edge_child[0], !st.edge_fwd[0]);
+      if (a.E.gi >= 0) { rc = CC_ERR_UNSUPPORTED; break; }  // pair-keyed: the cycle kernel's only
       int sE = a.E.p ? a.E.s : 2, sB = a.B.p ? a.B.s : 1, sA = a.A.p ? a.A.s : 1;
       a.sY = sE + sB - 1;
       a.RY = (int)binom(k - 1, a.sY - 1);
@@ -266,6 +418,7 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
         a.N[j] = tab_u(T, st.node_child[j]);
         a.E[j] = tab_e(T, st.edge_child[j], !st.edge_fwd[j]);
       }
+      if (any_pair(a.E, 3) || st.pair_out) { rc = CC_ERR_UNSUPPORTED; break; }
       a.nb = st.nb;
       for (int b = 0; b < st.nb; b++)
         for (int j = 0; j < 3; j++)
@@ -329,8 +482,11 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
       a.per_vertex = d_per_vertex;
       a.status = status;
       a.count_units = count_units;
+      if ((rc = bind_pairs(a, T)) != CC_OK) break;
       rc = launch_cycle(c, a);
       if (rc != CC_OK) c.scratch_dirty = c.hv_dirty = true;
+    } else if (st.kind == ST_CYCLE_NONROOT && st.nb == 2) {
+      rc = run_case2(c, g, gv, lut, B.colors, k, st, T, i, status, count_units);
     } else if (st.kind == ST_CYCLE_NONROOT && st.nb == 1) {
       // Case 1 block, L >= 4: its unary table by the image of the boundary
       // node, from the general kernel rooted there -- the cycle rotated so
@@ -359,9 +515,11 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
       a.per_vertex = nullptr;
       a.status = status;
       a.count_units = count_units;
+      a.out_mode = 1;
       a.out = T[i].p;
       a.R_out = R;
       a.s_out = st.s;
+      if ((rc = bind_pairs(a, T)) != CC_OK) break;
       rc = launch_cycle(c, a);
       if (rc != CC_OK) c.scratch_dirty = c.hv_dirty = true;
     } else if (st.kind == ST_ROOT_NODE) {
@@ -396,6 +554,8 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
 
 int status_code(const u64 *st) {
   if (st[ST_BOUNDS]) return CC_ERR_BOUNDS;
+  if (st[ST_BADGRAPH]) return CC_ERR_BAD_GRAPH;
+  if (st[ST_PAIRCAP]) return CC_ERR_OOM;
   if (st[ST_TIMEOUT] & 1ull) return CC_ERR_TIMEOUT;
   if (st[ST_TIMEOUT] & 2ull) return CC_ERR_UNSUPPORTED;
   if (st[ST_OVERFLOW]) return CC_ERR_OVERFLOW;
@@ -630,6 +790,17 @@ int cc_plan_inspect(int k, int n_edges, const int32_t *edges, const int32_t *blo
   }
   if (aut) *aut = p.aut;
   return w;
+}
+
+int cc_plan_supported(int k, int n_edges, const int32_t *edges, const int32_t *block_seq, int seq_len) {
+  if (n_edges < 0 || (n_edges > 0 && !edges) || seq_len < 0 || (seq_len > 0 && !block_seq)) return CC_ERR_INVALID_ARG;
+  std::vector<std::pair<int, int>> e;
+  for (int i = 0; i < n_edges; i++) e.push_back({edges[2 * i], edges[2 * i + 1]});
+  Plan p;
+  int rc = seq_len > 0 ? plan_explicit(k, e, std::vector<int>(block_seq, block_seq + seq_len), p)
+                       : plan_query(k, e, p);
+  if (rc == CC_ERR_UNSUPPORTED && !p.stages.empty()) return 0;
+  return rc == CC_OK ? 1 : rc;
 }
 
 int cc_plan_enumerate(int k, int n_edges, const int32_t *edges, int32_t *out, int cap, int *n_plans) {

@@ -226,7 +226,11 @@ extern "C" int cc_count_batch(cc_ctx *ctx, const cc_request *reqs, int n_reqs, u
     }
     // eager run: sizes the scratch and gives this call's results
     if (rc == CC_OK) rc = enqueue_batch(c, reqs, n_reqs, *b);
-    if (rc == CC_OK && c.capture) {
+    // a pass with a pair-keyed block sizes its pair list on the host: not capturable
+    bool host_sized = false;
+    for (int i = 0; i < n_reqs; i++)
+      for (auto &st : c.plans[reqs[i].query_id].stages) host_sized = host_sized || st.pair_out;
+    if (rc == CC_OK && c.capture && !host_sized) {
       // record the same sequence as a CUDA graph for later replays
       if (cudaStreamSynchronize(c.stream) != cudaSuccess) rc = CC_ERR_CUDA;
       c.timing = false;

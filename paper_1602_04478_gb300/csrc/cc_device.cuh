@@ -85,8 +85,9 @@ __device__ __forceinline__ unsigned long long warp_sum_ck(unsigned long long v, 
 // ST_SCAN0 + j: data edges scanned out of level j of a root cycle's halves
 // (structural counting only; a status block then has kStatusWords words).
 // ST_BOUNDS: an index outside its array (bounds-check build only).
+// ST_PAIRCAP: a Case-2 pair list outgrew the buffer sized by its count pass.
 enum { ST_COUNT = 0, ST_OVERFLOW = 1, ST_TIMEOUT = 2, ST_BADGRAPH = 3, ST_UNITS = 4, ST_MAXDEG = 5, ST_BOUNDS = 6,
-       ST_SCAN0 = 8 };
+       ST_PAIRCAP = 7, ST_SCAN0 = 8 };
 constexpr int kStatusWords = 16;
 
 // Bounds-check build (libcc_boundscheck.so, CC_BOUNDS_CHECK set): an index

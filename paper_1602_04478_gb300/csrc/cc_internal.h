@@ -13,6 +13,10 @@ namespace cc {
 
 constexpr int kMaxK = CC_MAX_K;
 constexpr int kMaxCycle = 8;  // longest root cycle the closure kernel handles
+constexpr int kMaxPairGraphs = 4;  // pair-keyed edge tables one cycle block may read
+// levels (hops) of the longer half the cycle kernel walks; a Case-2 block
+// cut at its boundary nodes has halves of d and L - d hops
+constexpr int kMaxHalf = kMaxCycle / 2 + 1;
 
 // ------------------------------- query plan -------------------------------
 enum StageKind { ST_LEAF = 0, ST_TRI = 1, ST_CYCLE_ROOT = 2, ST_ROOT_NODE = 3, ST_CYCLE_NONROOT = 4 };
@@ -27,6 +31,9 @@ struct Stage {
   int node_child[kMaxK];     // per position: stage index of the annotating block, -1 none
   int edge_child[kMaxK];     // per cycle edge nodes[i] -> nodes[i+1 mod L]
   bool edge_fwd[kMaxK];      // child's first boundary node is nodes[i]
+  // Case-2 table keyed by pairs that need not be data edges (the boundary
+  // nodes are not adjacent in the cycle, or joined by such an edge)
+  bool pair_out = false;
   int s = 0;                 // |SQ(B)|: query nodes of the represented subquery
   uint32_t sq_mask = 0;
   std::string sig;           // structure of the block's subtree: equal strings, equal tables
@@ -59,6 +66,10 @@ struct PlanChoice {
   double cost = 0;  // the library's engine-aware join cost
 };
 int plan_enumerate(int k, const std::vector<std::pair<int, int>> &edges, std::vector<PlanChoice> &out);
+// Edge i of stage g is annotated by a pair-keyed table (walked over its pair graph).
+inline bool edge_pair_keyed(const std::vector<Stage> &st, const Stage &g, int i) {
+  return g.edge_child[i] >= 0 && st[g.edge_child[i]].pair_out;
+}
 
 // Structural work of one stage of a colouring pass (independent of the
 // colouring): edge-subset updates, algorithmic bytes (the compulsory reads

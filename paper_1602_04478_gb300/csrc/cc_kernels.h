@@ -22,12 +22,18 @@ struct TabU {
   int R = 1;
 };
 // edge-keyed table [nnz][R] over size-s signatures; use_rev: the row of a
-// traversal x -> y is rev[pos(x -> y)] instead of pos(x -> y)
+// traversal x -> y is rev[pos(x -> y)] instead of pos(x -> y).
+// gi >= 0 (cycle kernel only): the table is keyed by the positions of the
+// pair graph pg[gi] of the cycle's arguments -- a Case-2 block whose boundary
+// images need not be adjacent in the data graph -- and the row of position q
+// is ridx[q] (-1: an all-zero row)
 struct TabE {
   const u64 *p = nullptr;
   int s = 2;
   int R = 1;
   bool use_rev = false;
+  int gi = -1;
+  const int64_t *ridx = nullptr;
 };
 
 struct LeafArgs {
@@ -94,12 +100,42 @@ struct CycleArgs {
   bool count_units = false;   // add the structural edge-subset work to status[ST_UNITS]
   int32_t light_end = 0;      // the per-CTA kernel takes sources of rank < light_end
   bool no_order = false;      // PS procedure: paths from u are not restricted to vertices below u
-  // non-root cycle with one boundary node at position 0 (no_order): the
-  // unary table [n][R_out] over signatures of size s_out, by the image u of
-  // the boundary node, instead of a count
+  // length of P+ (the cut nodes are a_h and a_{h+split}); 0: floor(L/2)
+  int split = 0;
+  // pair graphs of the pair-keyed edge tables (TabE::gi)
+  GraphView pg[kMaxPairGraphs];
+  // Non-root cycle (no_order, the first boundary node at position 0, its
+  // image u the source; signatures of size s_out, rows of R_out slots):
+  //   out_mode 1: one boundary node; the unary table [n][R_out] by u
+  //   out_mode 2: two boundary nodes a_0, a_1 (split 1, the pair is a data
+  //               edge); the edge-keyed table [nnz][R_out], row pos(u -> x)
+  //   out_mode 3: two boundary nodes a_0, a_split; every nonzero (u, x) row
+  //               appended to pair_keys (u << 32 | x) / pair_rows [][R_out]
+  //               (pair_keys null: only counted into *pair_count)
+  int out_mode = 0;
   u64 *out = nullptr;
   int R_out = 0, s_out = 0;
+  unsigned long long *pair_keys = nullptr;
+  u64 *pair_rows = nullptr;
+  unsigned long long *pair_count = nullptr;
+  int64_t pair_cap = 0;
 };
+// Pair graph of a Case-2 table: the symmetric closure of its (u, x) keys as a
+// CSR over the data graph's vertices (rows ascending), with rev and lo_cnt
+// like the data graph, and the row index of each position into the rows
+// (-1 where only the reverse pair has a row).  Built from the appended list.
+struct PairGraph {
+  int64_t n = 0, n_pairs = 0, nnz = 0;
+  int64_t *row = nullptr;
+  int32_t *col = nullptr;
+  int64_t *rev = nullptr;
+  int32_t *lo_cnt = nullptr;
+  int64_t *ridx = nullptr;
+  u64 *rows = nullptr;  // [n_pairs][R]
+  int R = 0;
+};
+int pair_graph_build(Ctx &c, int64_t n, const unsigned long long *keys, int64_t n_pairs, PairGraph &pg);
+void pair_graph_free(Ctx &c, PairGraph &pg);
 int run_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank, int B);
 bool plain_cycle_eligible(const CycleArgs &a);
 int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank);
@@ -123,6 +159,8 @@ struct Table {
   size_t bytes = 0;
   int arity = 0;  // 1 unary, 2 edge-keyed
   int s = 0, R = 0;
+  bool pair = false;  // pair-keyed (rows in pg.rows, built during the pass)
+  PairGraph pg;
 };
 struct PassBuffers {
   std::vector<Table> T;

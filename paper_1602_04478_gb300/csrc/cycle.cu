@@ -29,7 +29,7 @@ namespace cc {
 
 constexpr int kCtaThreads = 256;
 constexpr int kWarps = kCtaThreads / 32;
-constexpr int kMaxLevels = kMaxCycle / 2 + 1;
+constexpr int kMaxLevels = kMaxHalf;
 
 struct CycleScratch {
   char *base = nullptr;
@@ -61,7 +61,7 @@ struct LevelInfo {
 __device__ __host__ inline void level_info(const CycleArgs &a, int h, int half, int j, LevelInfo &out,
                                            int *depth_out) {
   int L = a.L;
-  int rp = L / 2, rm = L - L / 2;
+  int rp = a.split ? a.split : L / 2, rm = L - rp;
   int depth = half == 0 ? rp : rm;
   if (depth_out) *depth_out = depth;
   int s = half == 0 ? 1 : (a.N[h].p ? a.N[h].s : 1);
@@ -90,10 +90,25 @@ __device__ __host__ inline void level_info(const CycleArgs &a, int h, int half, 
   }
 }
 
-// End of the part of v's row a path from source u may extend into: the
-// vertices below u (DB, rows are rank ordered), or the whole row (PS).
-__device__ __forceinline__ int64_t row_end(const CycleArgs &a, int64_t vb, int32_t v, int32_t u) {
-  return a.no_order ? a.g.row[v + 1] : lower_bound_i32(a.g.col, vb, a.g.row[v + 1], u);
+// End of the part of v's row (in graph g) a path from source u may extend
+// into: the vertices below u (DB, rows are rank ordered), or the whole row
+// (PS and non-root blocks).
+__device__ __forceinline__ int64_t row_end(const CycleArgs &a, const GraphView &g, int64_t vb, int32_t v,
+                                           int32_t u) {
+  return a.no_order ? g.row[v + 1] : lower_bound_i32(g.col, vb, g.row[v + 1], u);
+}
+
+// The graph a hop over an edge with table E walks: the data graph, or the
+// pair graph of a pair-keyed table (its rows hold the partners x of u).
+__device__ __forceinline__ GraphView walk_graph(const CycleArgs &a, const TabE &E) {
+  return E.gi >= 0 ? a.pg[E.gi] : a.g;
+}
+
+// Row of an edge-keyed table for walk position epos (null: all zero).
+__device__ __forceinline__ const u64 *erow_of(const TabE &E, int64_t epos) {
+  if (!E.ridx) return E.p + epos * E.R;
+  const int64_t r = __ldg(E.ridx + epos);
+  return r < 0 ? nullptr : E.p + r * E.R;
 }
 
 __device__ __forceinline__ int rows_of(int k, int s) {
@@ -164,7 +179,8 @@ __device__ __forceinline__ void extend_row(const Lut &lut, const u64 *src, int s
     }
     return;
   }
-  const u64 *erow = E.p + epos * E.R;
+  const u64 *erow = erow_of(E, epos);
+  if (!erow) return;
   for (int l = 0; l < E.R; l++) {
     u64 t = __ldg(erow + l);
     if (!t) continue;
@@ -203,6 +219,36 @@ __device__ SlotPtrs slot_ptrs(const CycleScratch &sc, int slot) {
   return p;
 }
 
+// Last hop w -> x of one half into acc (pair rows (u, x) of P+ or P-): w is
+// a vertex of x's row in the hop's graph gg at CSR position e; lv is the
+// half's last materialised level (0: the half is the single edge u -> x and
+// its start row is {chi(u)}).
+__device__ __forceinline__ void pull_hop(const CycleArgs &a, const GraphView &gg, const SlotPtrs &P,
+                                         const CycleScratch &sc, unsigned long long cur, int hs, int lv,
+                                         const LevelInfo &last, int s_prev, int R_prev, int64_t e, int32_t w,
+                                         int cw, int32_t u, int cu, int cx, u64 *acc, unsigned &ovf) {
+  // traversal w -> x: its CSR position is rev[e]
+  if (lv == 0) {
+    if (w != u) return;
+    if (!last.E.p) {
+      atomic_add_ck(acc + pslot(a.lut, (1u << cu) | (1u << cx), cu, cx), 1ull, ovf);
+      return;
+    }
+    const u64 *er = erow_of(last.E, last.E.use_rev ? e : __ldg(gg.rev + e));
+    if (!er) return;
+    for (int l = 0; l < last.E.R; l++) {
+      const u64 t = __ldg(er + l);
+      if (!t) continue;
+      atomic_add_ck(acc + pslot(a.lut, pmask(a.lut, last.E.s, l, cu, cx), cu, cx), t, ovf);
+    }
+    return;
+  }
+  if (!stamp_has(P.stamp, w, cur, hs * kMaxLevels + lv)) return;
+  const int64_t ep = last.E.p ? (last.E.use_rev ? e : __ldg(gg.rev + e)) : 0;
+  extend_row(a.lut, P.rows[hs][lv] + (int64_t)w * sc.rstride[hs][lv], s_prev, R_prev, last.E, ep, cu, cw, cx, acc,
+             ovf);
+}
+
 __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch sc, int *work_counter) {
   extern __shared__ u64 smem_acc[];
   __shared__ int s_u;
@@ -215,11 +261,14 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
   SlotPtrs P = slot_ptrs(sc, blockIdx.x);
   u64 *accP = smem_acc + (size_t)wib * 2 * sc.acc_stride;
   u64 *accM = accP + sc.acc_stride;
-  // unary output (non-root cycle): the current source's row, gathered here
-  unsigned long long *orow = smem_acc + (size_t)kWarps * 2 * sc.acc_stride;
-  for (int i = tid; i < (a.out ? a.R_out : 0); i += kCtaThreads) orow[i] = 0;
+  // output rows gathered in shared memory: out_mode 1, the current source's
+  // row (one per CTA); out_mode 2 and 3, the (u, x) row of each warp
+  unsigned long long *obase = smem_acc + (size_t)kWarps * 2 * sc.acc_stride;
+  unsigned long long *orow = a.out_mode >= 2 ? obase + (size_t)wib * a.R_out : obase;
+  const int o_all = a.out_mode == 0 ? 0 : (a.out_mode == 1 ? a.R_out : kWarps * a.R_out);
+  for (int i = tid; i < o_all; i += kCtaThreads) obase[i] = 0;
   unsigned ovf = 0;
-  const int rp = L / 2, rm = L - L / 2;
+  const int rp = a.split ? a.split : L / 2, rm = L - rp;
   while (true) {
     if (tid == 0) {
       // once a count of this pass has exceeded 2^64-1 the result is fixed
@@ -232,293 +281,345 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
     __syncthreads();
     const int32_t u = s_u;
     if (u < 0) break;
-    const int64_t ub = a.g.row[u];
-    // DB: the lower neighbours (a row prefix); PS: every neighbour
-    const int du = a.no_order ? (int)(a.g.row[u + 1] - ub) : a.g.lo_cnt[u];
     const int cu = a.colors[u];
-    if (du >= 2) {
-      for (int hi = 0; hi < a.n_h; hi++) {
-        const int h = a.hs[hi];
-        // stamps are cleared after every (source, h), so (u, h) is a unique key
-        const unsigned long long cur = ((unsigned long long)(u + 1) << 3) | (unsigned)hi;
-        // levels each half materialises; with a shared chain half 0 carries both
-        int mat[2] = {rp - 1, rm - 1};
-        if (sc.shared_chain) {
-          mat[0] = max(rp - 1, rm - 1);
-          mat[1] = 0;
+    bool wrote = false;
+    for (int hi = 0; hi < a.n_h; hi++) {
+      const int h = a.hs[hi];
+      LevelInfo f0, f1;
+      level_info(a, h, 0, 1, f0, nullptr);
+      level_info(a, h, 1, 1, f1, nullptr);
+      // the first hop of each half: u's row (its lower part under DB) in the hop's graph
+      const GraphView g0 = walk_graph(a, f0.E), g1 = walk_graph(a, f1.E);
+      const int64_t ub0 = g0.row[u], ub1 = g1.row[u];
+      const int du0 = a.no_order ? (int)(g0.row[u + 1] - ub0) : g0.lo_cnt[u];
+      const int du1 = a.no_order ? (int)(g1.row[u + 1] - ub1) : g1.lo_cnt[u];
+      // both halves leave u, over two distinct vertices when they walk one graph
+      if (du0 < 1 || du1 < 1 || (g0.row == g1.row && du0 < 2)) continue;
+      wrote = true;
+      // stamps are cleared after every (source, h), so (u, h) is a unique key
+      const unsigned long long cur = ((unsigned long long)(u + 1) << 3) | (unsigned)hi;
+      // levels each half materialises; with a shared chain half 0 carries both
+      int mat[2] = {rp - 1, rm - 1};
+      if (sc.shared_chain) {
+        mat[0] = max(rp - 1, rm - 1);
+        mat[1] = 0;
+      }
+      if (tid < 2 * kMaxLevels + 1) s_cnt[tid] = 0;
+      __syncthreads();
+      // ---- level 1: the first hop of each half ----
+      for (int hf = 0; hf < 2; hf++) {
+        if (mat[hf] < 1) continue;
+        const LevelInfo &li = hf == 0 ? f0 : f1;
+        const GraphView &gf = hf == 0 ? g0 : g1;
+        const int64_t ub = hf == 0 ? ub0 : ub1;
+        const int du = hf == 0 ? du0 : du1;
+        for (int i = tid; i < du; i += kCtaThreads) {
+          const int32_t v = __ldg(gf.col + ub + i);
+          const int cv = a.colors[v];
+          P.list[hf][1][i] = v;
+          stamp_set(P.stamp, v, cur, hf * kMaxLevels + 1);
+          if (cv == cu) continue;
+          u64 *dst = li.join ? P.pre[hf][1] + (int64_t)v * sc.pstride[hf][1]
+                             : P.rows[hf][1] + (int64_t)v * sc.rstride[hf][1];
+          // start row: source node block (P- only) joined with the first edge
+          int s0 = hf == 0 ? 1 : (a.N[h].p ? a.N[h].s : 1);
+          const TabE &E = li.E;
+          const u64 *erow = nullptr;
+          if (E.p) {
+            erow = erow_of(E, E.use_rev ? __ldg(gf.rev + ub + i) : ub + i);
+            if (!erow) continue;
+          }
+          const u64 *nrow = (hf == 1 && a.N[h].p) ? a.N[h].p + (int64_t)u * a.N[h].R : nullptr;
+          int n0 = nrow ? a.N[h].R : 1;
+          int nE = E.p ? E.R : 1;
+          for (int j0 = 0; j0 < n0; j0++) {
+            u64 v0 = nrow ? __ldg(nrow + j0) : 1ull;
+            if (!v0) continue;
+            uint32_t m0 = nrow ? umask(a.lut, s0, j0, cu) : (1u << cu);
+            for (int je = 0; je < nE; je++) {
+              u64 ve = erow ? __ldg(erow + je) : 1ull;
+              if (!ve) continue;
+              uint32_t me = E.p ? pmask(a.lut, E.s, je, cu, cv) : ((1u << cu) | (1u << cv));
+              if ((m0 & me) != (1u << cu)) continue;
+              u64 val = mul_ck(v0, ve, ovf);
+              u64 *d = dst + pslot(a.lut, m0 | me, cu, cv);
+              *d = add_ck(*d, val, ovf);
+            }
+          }
         }
-        if (tid < 2 * kMaxLevels + 1) s_cnt[tid] = 0;
-        __syncthreads();
-        // ---- level 1: lower neighbours of u ----
+        if (tid == 0) s_cnt[hf * kMaxLevels + 1] = du;
+      }
+      if (a.count_units && tid == 0) {
+        // extension out of level 0 for both halves: the first hops times the start row's slots
+        u64 r0 = 1 + (u64)(a.N[h].p ? a.N[h].R : 1);
+        atomicAdd(a.status + ST_UNITS, (u64)(du0 + du1) / 2 * r0);
+        atomicAdd(a.status + ST_SCAN0, (u64)du0 + (u64)du1);
+      }
+      __syncthreads();
+      // node joins at level 1
+      for (int hf = 0; hf < 2; hf++) {
+        if (mat[hf] < 1) continue;
+        const LevelInfo &li = hf == 0 ? f0 : f1;
+        if (!li.join) continue;
+        const int Rp = rows_of(k, li.s_pre);
+        const int du = hf == 0 ? du0 : du1;
+        for (int i = wib; i < du; i += kWarps) {
+          int32_t v = P.list[hf][1][i];
+          join_node(a.lut, P.pre[hf][1] + (int64_t)v * sc.pstride[hf][1], li.s_pre, Rp, li.N, v, cu, a.colors[v],
+                    P.rows[hf][1] + (int64_t)v * sc.rstride[hf][1], li.s, ovf, lane, true);
+        }
+      }
+      __syncthreads();
+      // ---- pushes: level j -> j+1 ----
+      const int maxmat = max(mat[0], mat[1]);
+      for (int j = 1; j < maxmat; j++) {
         for (int hf = 0; hf < 2; hf++) {
-          if (mat[hf] < 1) continue;
-          LevelInfo li;
-          level_info(a, h, hf, 1, li, nullptr);
-          const int Rp = rows_of(k, li.s_pre), R = rows_of(k, li.s);
-          for (int i = tid; i < du; i += kCtaThreads) {
-            const int32_t v = __ldg(a.g.col + ub + i);
-            const int cv = a.colors[v];
-            P.list[hf][1][i] = v;
-            stamp_set(P.stamp, v, cur, hf * kMaxLevels + 1);
-            if (cv == cu) continue;
-            u64 *dst = li.join ? P.pre[hf][1] + (int64_t)v * sc.pstride[hf][1]
-                               : P.rows[hf][1] + (int64_t)v * sc.rstride[hf][1];
-            // start row: source node block (P- only) joined with the first edge
-            int s0 = hf == 0 ? 1 : (a.N[h].p ? a.N[h].s : 1);
-            const TabE &E = li.E;
-            int64_t epos = E.use_rev ? __ldg(a.g.rev + ub + i) : ub + i;
-            const u64 *nrow = (hf == 1 && a.N[h].p) ? a.N[h].p + (int64_t)u * a.N[h].R : nullptr;
-            int n0 = nrow ? a.N[h].R : 1;
-            int nE = E.p ? E.R : 1;
-            for (int j0 = 0; j0 < n0; j0++) {
-              u64 v0 = nrow ? __ldg(nrow + j0) : 1ull;
-              if (!v0) continue;
-              uint32_t m0 = nrow ? umask(a.lut, s0, j0, cu) : (1u << cu);
-              for (int je = 0; je < nE; je++) {
-                u64 ve = E.p ? __ldg(E.p + epos * E.R + je) : 1ull;
-                if (!ve) continue;
-                uint32_t me = E.p ? pmask(a.lut, E.s, je, cu, cv) : ((1u << cu) | (1u << cv));
-                if ((m0 & me) != (1u << cu)) continue;
-                u64 val = mul_ck(v0, ve, ovf);
-                u64 *d = dst + pslot(a.lut, m0 | me, cu, cv);
-                *d = add_ck(*d, val, ovf);
-              }
-            }
-            (void)Rp;
-            (void)R;
-          }
-          if (tid == 0) s_cnt[hf * kMaxLevels + 1] = du;
-        }
-        if (a.count_units && tid == 0) {
-          // extension out of level 0 for both halves: du edges times the start row's slots
-          u64 r0 = 1 + (u64)(a.N[h].p ? a.N[h].R : 1);
-          atomicAdd(a.status + ST_UNITS, (u64)du * r0);
-          atomicAdd(a.status + ST_SCAN0, 2ull * (u64)du);
-        }
-        __syncthreads();
-        // node joins at level 1
-        for (int hf = 0; hf < 2; hf++) {
-          if (mat[hf] < 1) continue;
-          LevelInfo li;
-          level_info(a, h, hf, 1, li, nullptr);
-          if (!li.join) continue;
-          const int Rp = rows_of(k, li.s_pre);
-          for (int i = wib; i < du; i += kWarps) {
-            int32_t v = P.list[hf][1][i];
-            join_node(a.lut, P.pre[hf][1] + (int64_t)v * sc.pstride[hf][1], li.s_pre, Rp, li.N, v, cu,
-                      a.colors[v], P.rows[hf][1] + (int64_t)v * sc.rstride[hf][1], li.s, ovf, lane, true);
-          }
-        }
-        __syncthreads();
-        // ---- pushes: level j -> j+1 ----
-        const int maxmat = max(mat[0], mat[1]);
-        for (int j = 1; j < maxmat; j++) {
-          for (int hf = 0; hf < 2; hf++) {
-            if (mat[hf] < j + 1) continue;
-            LevelInfo lj, ln;
-            level_info(a, h, hf, j, lj, nullptr);
-            level_info(a, h, hf, j + 1, ln, nullptr);
-            const int Rj = rows_of(k, lj.s);
-            const int cnt = s_cnt[hf * kMaxLevels + j];
-            u64 *dstbase = ln.join ? P.pre[hf][j + 1] : P.rows[hf][j + 1];
-            const int dstride = ln.join ? sc.pstride[hf][j + 1] : sc.rstride[hf][j + 1];
-            for (int i = wib; i < cnt; i += kWarps) {
-              const int32_t v = P.list[hf][j][i];
-              const int cv = a.colors[v];
-              const u64 *src = P.rows[hf][j] + (int64_t)v * sc.rstride[hf][j];
-              const int64_t vb = a.g.row[v];
-              const int64_t ve = row_end(a, vb, v, u);
-              for (int64_t e = vb + lane; e < ve; e += 32) {
-                const int32_t w = __ldg(a.g.col + e);
-                if (stamp_set(P.stamp, w, cur, hf * kMaxLevels + j + 1)) {
-                  int slot = atomicAdd(&s_cnt[hf * kMaxLevels + j + 1], 1);
-                  P.list[hf][j + 1][slot] = w;
-                }
-                int64_t epos = ln.E.use_rev ? __ldg(a.g.rev + e) : e;
-                extend_row(a.lut, src, lj.s, Rj, ln.E, epos, cu, cv, a.colors[w],
-                           dstbase + (int64_t)w * dstride, ovf);
-              }
-            }
-          }
-          __syncthreads();
-          for (int hf = 0; hf < 2; hf++) {
-            if (mat[hf] < j + 1) continue;
-            LevelInfo ln;
-            level_info(a, h, hf, j + 1, ln, nullptr);
-            if (!ln.join) continue;
-            const int cnt = s_cnt[hf * kMaxLevels + j + 1];
-            const int Rp = rows_of(k, ln.s_pre);
-            for (int i = wib; i < cnt; i += kWarps) {
-              int32_t w = P.list[hf][j + 1][i];
-              join_node(a.lut, P.pre[hf][j + 1] + (int64_t)w * sc.pstride[hf][j + 1], ln.s_pre, Rp, ln.N, w, cu,
-                        a.colors[w], P.rows[hf][j + 1] + (int64_t)w * sc.rstride[hf][j + 1], ln.s, ovf, lane,
-                        true);
-            }
-          }
-          __syncthreads();
-        }
-        if (a.count_units) {
-          for (int hf = 0; hf < 2; hf++) {
-            const int depth = hf == 0 ? rp : rm;
-            const int hsl = sc.shared_chain ? 0 : hf;
-            for (int j = 1; j < depth; j++) {
-              LevelInfo lj;
-              level_info(a, h, hf, j, lj, nullptr);
-              const u64 Rj = (u64)rows_of(k, lj.s);
-              const int cnt = s_cnt[hsl * kMaxLevels + j];
-              u64 acc = 0, edges = 0;
-              for (int i = tid; i < cnt; i += kCtaThreads) {
-                const int32_t v = P.list[hsl][j][i];
-                const int64_t vb = a.g.row[v];
-                const u64 e = (u64)(row_end(a, vb, v, u) - vb);
-                acc += e * Rj;
-                edges += e;
-              }
-              if (acc) atomicAdd(a.status + ST_UNITS, acc);
-              if (edges && j < 8) atomicAdd(a.status + ST_SCAN0 + j, edges);
-            }
-          }
-        }
-        // ---- candidate meeting vertices: neighbours (below u) of the smaller last level ----
-        int hsrc[2] = {0, sc.shared_chain ? 0 : 1};
-        int lsrc[2] = {rp - 1, rm - 1};
-        int pick = 0;
-        {
-          int c0 = s_cnt[hsrc[0] * kMaxLevels + lsrc[0]];
-          int c1 = s_cnt[hsrc[1] * kMaxLevels + lsrc[1]];
-          pick = (c1 < c0) ? 1 : 0;
-        }
-        {
-          const int hf = hsrc[pick], lv = lsrc[pick];
-          const int cnt = s_cnt[hf * kMaxLevels + lv];
+          if (mat[hf] < j + 1) continue;
+          LevelInfo lj, ln;
+          level_info(a, h, hf, j, lj, nullptr);
+          level_info(a, h, hf, j + 1, ln, nullptr);
+          const GraphView gw = walk_graph(a, ln.E);
+          const int Rj = rows_of(k, lj.s);
+          const int cnt = s_cnt[hf * kMaxLevels + j];
+          u64 *dstbase = ln.join ? P.pre[hf][j + 1] : P.rows[hf][j + 1];
+          const int dstride = ln.join ? sc.pstride[hf][j + 1] : sc.rstride[hf][j + 1];
           for (int i = wib; i < cnt; i += kWarps) {
-            const int32_t v = P.list[hf][lv][i];
-            const int64_t vb = a.g.row[v];
-            const int64_t ve = row_end(a, vb, v, u);
+            const int32_t v = P.list[hf][j][i];
+            const int cv = a.colors[v];
+            const u64 *src = P.rows[hf][j] + (int64_t)v * sc.rstride[hf][j];
+            const int64_t vb = gw.row[v];
+            const int64_t ve = row_end(a, gw, vb, v, u);
             for (int64_t e = vb + lane; e < ve; e += 32) {
-              const int32_t x = __ldg(a.g.col + e);
-              if (stamp_set(P.stamp, x, cur, 2 * kMaxLevels)) {
-                int slot = atomicAdd(&s_cnt[2 * kMaxLevels], 1);
-                P.xlist[slot] = x;
+              const int32_t w = __ldg(gw.col + e);
+              if (stamp_set(P.stamp, w, cur, hf * kMaxLevels + j + 1)) {
+                int slot = atomicAdd(&s_cnt[hf * kMaxLevels + j + 1], 1);
+                P.list[hf][j + 1][slot] = w;
               }
+              int64_t epos = ln.E.use_rev ? __ldg(gw.rev + e) : e;
+              extend_row(a.lut, src, lj.s, Rj, ln.E, epos, cu, cv, a.colors[w], dstbase + (int64_t)w * dstride,
+                         ovf);
             }
           }
         }
         __syncthreads();
-        // ---- pull both halves at x and close ----
-        {
-          LevelInfo lp_last, lm_last, lp_prev, lm_prev;
-          level_info(a, h, 0, rp, lp_last, nullptr);
-          level_info(a, h, 1, rm, lm_last, nullptr);
-          level_info(a, h, 0, rp - 1, lp_prev, nullptr);
-          level_info(a, h, 1, rm - 1, lm_prev, nullptr);
-          const int RPpre = rows_of(k, lp_last.s_pre), RM = rows_of(k, lm_last.s_pre);
-          const int RPprev = rows_of(k, lp_prev.s), RMprev = rows_of(k, lm_prev.s);
-          const int xc = s_cnt[2 * kMaxLevels];
-          const int hp = hsrc[0], hm = hsrc[1];
-          u64 mine = 0;
-          for (int i = wib; i < xc; i += kWarps) {
-            const int32_t x = P.xlist[i];
-            const int cx = a.colors[x];
-            for (int t = lane; t < RPpre; t += 32) accP[t] = 0;
-            for (int t = lane; t < RM; t += 32) accM[t] = 0;
-            __syncwarp();
-            if (cx != cu) {
-              const int64_t xb = a.g.row[x];
-              const int64_t xe = row_end(a, xb, x, u);
-              for (int64_t e = xb + lane; e < xe; e += 32) {
-                const int32_t w = __ldg(a.g.col + e);
-                const int cw = a.colors[w];
-                // traversal w -> x: its CSR position is rev[e]
-                if (stamp_has(P.stamp, w, cur, hp * kMaxLevels + rp - 1)) {
-                  int64_t ep = lp_last.E.p ? (lp_last.E.use_rev ? e : __ldg(a.g.rev + e)) : 0;
-                  extend_row(a.lut, P.rows[hp][rp - 1] + (int64_t)w * sc.rstride[hp][rp - 1], lp_prev.s, RPprev,
-                             lp_last.E, ep, cu, cw, cx, accP, ovf);
-                }
-                if (stamp_has(P.stamp, w, cur, hm * kMaxLevels + rm - 1)) {
-                  int64_t ep = lm_last.E.p ? (lm_last.E.use_rev ? e : __ldg(a.g.rev + e)) : 0;
-                  extend_row(a.lut, P.rows[hm][rm - 1] + (int64_t)w * sc.rstride[hm][rm - 1], lm_prev.s, RMprev,
-                             lm_last.E, ep, cu, cw, cx, accM, ovf);
-                }
-              }
-            }
-            __syncwarp();
-            if (cx != cu) {
-              // closure: (P+ at x, joined with a_d's block) x (P- at x)
-              const u64 *nrow = lp_last.join ? lp_last.N.p + (int64_t)x * lp_last.N.R : nullptr;
-              const int nN = nrow ? lp_last.N.R : 1;
-              for (int t = lane; t < RPpre; t += 32) {
-                u64 vp = accP[t];
-                if (!vp) continue;
-                uint32_t mp = pmask(a.lut, lp_last.s_pre, t, cu, cx);
-                for (int l = 0; l < nN; l++) {
-                  u64 vn = nrow ? __ldg(nrow + l) : 1ull;
-                  if (!vn) continue;
-                  uint32_t mn = nrow ? umask(a.lut, lp_last.N.s, l, cx) : (1u << cx);
-                  if ((mp & mn) != (1u << cx)) continue;
-                  uint32_t m1 = mp | mn;
-                  if (a.out) {
-                    // non-root block: every P- signature meeting m1 in {chi(u), chi(x)};
-                    // the union is the block's signature, counted at u's row
-                    const u64 vpn = mul_ck(vp, vn, ovf);
-                    for (int t2 = 0; t2 < RM; t2++) {
-                      const u64 vm = accM[t2];
-                      if (!vm) continue;
-                      const uint32_t mm = pmask(a.lut, lm_last.s_pre, t2, cu, cx);
-                      if ((m1 & mm) != ((1u << cu) | (1u << cx))) continue;
-                      const u64 v = mul_ck(vpn, vm, ovf);
-                      const int slot = uslot(a.lut, m1 | mm, cu);
-                      if (!cc_in(slot, a.R_out, a.status)) continue;
-                      const unsigned long long old = atomicAdd(orow + slot, v);
-                      ovf |= (old + v < old);
-                    }
-                    continue;
-                  }
-                  uint32_t m2 = (K & ~m1) | (1u << cu) | (1u << cx);
-                  u64 vm = accM[pslot(a.lut, m2, cu, cx)];
-                  if (!vm) continue;
-                  mine = add_ck(mine, mul_ck(mul_ck(vp, vn, ovf), vm, ovf), ovf);
-                }
-              }
-            }
-            __syncwarp();
+        for (int hf = 0; hf < 2; hf++) {
+          if (mat[hf] < j + 1) continue;
+          LevelInfo ln;
+          level_info(a, h, hf, j + 1, ln, nullptr);
+          if (!ln.join) continue;
+          const int cnt = s_cnt[hf * kMaxLevels + j + 1];
+          const int Rp = rows_of(k, ln.s_pre);
+          for (int i = wib; i < cnt; i += kWarps) {
+            int32_t w = P.list[hf][j + 1][i];
+            join_node(a.lut, P.pre[hf][j + 1] + (int64_t)w * sc.pstride[hf][j + 1], ln.s_pre, Rp, ln.N, w, cu,
+                      a.colors[w], P.rows[hf][j + 1] + (int64_t)w * sc.rstride[hf][j + 1], ln.s, ovf, lane, true);
           }
-          mine = warp_sum_ck(mine, ovf);
-          if (lane == 0 && mine) {
-            unsigned long long old = atomicAdd(&s_total, mine);
-            if (old + mine < old) ovf |= 1u;
-          }
-        }
-        __syncthreads();
-        // ---- clear the rows and stamps this source touched (scratch returns to zero) ----
-        for (int hf = 0; hf < 2; hf++)
-          for (int j = 1; j <= mat[hf]; j++) {
-            const int cnt = s_cnt[hf * kMaxLevels + j];
-            const int rs = sc.rstride[hf][j], ps = sc.pstride[hf][j];
-            for (int i = tid; i < cnt; i += kCtaThreads) {
-              int32_t w = P.list[hf][j][i];
-              P.list[hf][j][i] = 0;
-              u64 *r = P.rows[hf][j] + (int64_t)w * rs;
-              for (int t = 0; t < rs; t++) r[t] = 0;
-              if (ps) {
-                u64 *q = P.pre[hf][j] + (int64_t)w * ps;
-                for (int t = 0; t < ps; t++) q[t] = 0;
-              }
-              P.stamp[w] = 0;
-            }
-          }
-        for (int i = tid; i < s_cnt[2 * kMaxLevels]; i += kCtaThreads) {
-          P.stamp[P.xlist[i]] = 0;
-          P.xlist[i] = 0;
         }
         __syncthreads();
       }
-      if (a.out) {
-        // u's row of the non-root block's table (only this CTA writes it)
-        for (int i = tid; i < a.R_out; i += kCtaThreads) {
-          a.out[(int64_t)u * a.R_out + i] = orow[i];
-          orow[i] = 0;
+      if (a.count_units) {
+        for (int hf = 0; hf < 2; hf++) {
+          const int depth = hf == 0 ? rp : rm;
+          const int hsl = sc.shared_chain ? 0 : hf;
+          for (int j = 1; j < depth; j++) {
+            LevelInfo lj, ln;
+            level_info(a, h, hf, j, lj, nullptr);
+            level_info(a, h, hf, j + 1, ln, nullptr);
+            const GraphView gw = walk_graph(a, ln.E);
+            const u64 Rj = (u64)rows_of(k, lj.s);
+            const int cnt = s_cnt[hsl * kMaxLevels + j];
+            u64 acc = 0, edges = 0;
+            for (int i = tid; i < cnt; i += kCtaThreads) {
+              const int32_t v = P.list[hsl][j][i];
+              const int64_t vb = gw.row[v];
+              const u64 e = (u64)(row_end(a, gw, vb, v, u) - vb);
+              acc += e * Rj;
+              edges += e;
+            }
+            if (acc) atomicAdd(a.status + ST_UNITS, acc);
+            if (edges && j < 8) atomicAdd(a.status + ST_SCAN0 + j, edges);
+          }
         }
+      }
+      LevelInfo lp_last, lm_last, lp_prev, lm_prev;
+      level_info(a, h, 0, rp, lp_last, nullptr);
+      level_info(a, h, 1, rm, lm_last, nullptr);
+      if (rp > 1) level_info(a, h, 0, rp - 1, lp_prev, nullptr);
+      level_info(a, h, 1, rm - 1, lm_prev, nullptr);
+      // the last hop of each half walks its own graph
+      const GraphView gP = walk_graph(a, lp_last.E), gM = walk_graph(a, lm_last.E);
+      // ---- candidate meeting vertices: the last hop out of the smaller last level ----
+      int hsrc[2] = {0, sc.shared_chain ? 0 : 1};
+      int lsrc[2] = {rp - 1, rm - 1};
+      int pick = 0;
+      {
+        int c0 = lsrc[0] == 0 ? 1 : s_cnt[hsrc[0] * kMaxLevels + lsrc[0]];
+        int c1 = s_cnt[hsrc[1] * kMaxLevels + lsrc[1]];
+        pick = (c1 < c0) ? 1 : 0;
+      }
+      {
+        const int hf = hsrc[pick], lv = lsrc[pick];
+        const GraphView &gc = pick == 0 ? gP : gM;
+        const int cnt = lv == 0 ? 1 : s_cnt[hf * kMaxLevels + lv];
+        for (int i = wib; i < cnt; i += kWarps) {
+          const int32_t v = lv == 0 ? u : P.list[hf][lv][i];
+          const int64_t vb = gc.row[v];
+          const int64_t ve = row_end(a, gc, vb, v, u);
+          for (int64_t e = vb + lane; e < ve; e += 32) {
+            const int32_t x = __ldg(gc.col + e);
+            if (stamp_set(P.stamp, x, cur, 2 * kMaxLevels)) {
+              int slot = atomicAdd(&s_cnt[2 * kMaxLevels], 1);
+              P.xlist[slot] = x;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      // ---- pull both halves at x and close ----
+      {
+        const int RPpre = rows_of(k, lp_last.s_pre), RM = rows_of(k, lm_last.s_pre);
+        const int sPprev = rp > 1 ? lp_prev.s : 1;
+        const int RPprev = rp > 1 ? rows_of(k, lp_prev.s) : 0, RMprev = rows_of(k, lm_prev.s);
+        const int xc = s_cnt[2 * kMaxLevels];
+        const int hp = hsrc[0], hm = hsrc[1];
+        const bool one_walk = gP.row == gM.row;
+        u64 mine = 0;
+        for (int i = wib; i < xc; i += kWarps) {
+          const int32_t x = P.xlist[i];
+          const int cx = a.colors[x];
+          for (int t = lane; t < RPpre; t += 32) accP[t] = 0;
+          for (int t = lane; t < RM; t += 32) accM[t] = 0;
+          __syncwarp();
+          if (cx != cu) {
+            const int64_t xb = gP.row[x];
+            const int64_t xe = row_end(a, gP, xb, x, u);
+            for (int64_t e = xb + lane; e < xe; e += 32) {
+              const int32_t w = __ldg(gP.col + e);
+              const int cw = a.colors[w];
+              pull_hop(a, gP, P, sc, cur, hp, rp - 1, lp_last, sPprev, RPprev, e, w, cw, u, cu, cx, accP, ovf);
+              if (one_walk)
+                pull_hop(a, gM, P, sc, cur, hm, rm - 1, lm_last, lm_prev.s, RMprev, e, w, cw, u, cu, cx, accM, ovf);
+            }
+            if (!one_walk) {
+              const int64_t mb = gM.row[x];
+              const int64_t me = row_end(a, gM, mb, x, u);
+              for (int64_t e = mb + lane; e < me; e += 32) {
+                const int32_t w = __ldg(gM.col + e);
+                pull_hop(a, gM, P, sc, cur, hm, rm - 1, lm_last, lm_prev.s, RMprev, e, w, a.colors[w], u, cu, cx,
+                         accM, ovf);
+              }
+            }
+          }
+          __syncwarp();
+          if (cx != cu) {
+            // closure: (P+ at x, joined with a_d's block) x (P- at x)
+            const u64 *nrow = lp_last.join ? lp_last.N.p + (int64_t)x * lp_last.N.R : nullptr;
+            const int nN = nrow ? lp_last.N.R : 1;
+            for (int t = lane; t < RPpre; t += 32) {
+              u64 vp = accP[t];
+              if (!vp) continue;
+              uint32_t mp = pmask(a.lut, lp_last.s_pre, t, cu, cx);
+              for (int l = 0; l < nN; l++) {
+                u64 vn = nrow ? __ldg(nrow + l) : 1ull;
+                if (!vn) continue;
+                uint32_t mn = nrow ? umask(a.lut, lp_last.N.s, l, cx) : (1u << cx);
+                if ((mp & mn) != (1u << cx)) continue;
+                uint32_t m1 = mp | mn;
+                if (a.out_mode) {
+                  // non-root block: every P- signature meeting m1 in {chi(u), chi(x)};
+                  // the union is the block's signature, counted at u's row
+                  // (one boundary node) or at the (u, x) row (two)
+                  const u64 vpn = mul_ck(vp, vn, ovf);
+                  for (int t2 = 0; t2 < RM; t2++) {
+                    const u64 vm = accM[t2];
+                    if (!vm) continue;
+                    const uint32_t mm = pmask(a.lut, lm_last.s_pre, t2, cu, cx);
+                    if ((m1 & mm) != ((1u << cu) | (1u << cx))) continue;
+                    const u64 v = mul_ck(vpn, vm, ovf);
+                    const int slot = a.out_mode == 1 ? uslot(a.lut, m1 | mm, cu) : pslot(a.lut, m1 | mm, cu, cx);
+                    if (!cc_in(slot, a.R_out, a.status)) continue;
+                    const unsigned long long old = atomicAdd(orow + slot, v);
+                    ovf |= (old + v < old);
+                  }
+                  continue;
+                }
+                uint32_t m2 = (K & ~m1) | (1u << cu) | (1u << cx);
+                u64 vm = accM[pslot(a.lut, m2, cu, cx)];
+                if (!vm) continue;
+                mine = add_ck(mine, mul_ck(mul_ck(vp, vn, ovf), vm, ovf), ovf);
+              }
+            }
+          }
+          __syncwarp();
+          if (a.out_mode >= 2) {
+            // the warp's (u, x) row of a two-boundary block goes out if nonzero
+            bool any = false;
+            for (int t = lane; t < a.R_out; t += 32) any |= orow[t] != 0ull;
+            if (__any_sync(0xffffffffu, any)) {
+              int64_t dst = -1;
+              if (a.out_mode == 2) {
+                // the boundary pair is the edge u -> x of the data graph
+                if (lane == 0) {
+                  const int64_t q = lower_bound_i32(a.g.col, a.g.row[u], a.g.row[u + 1], x);
+                  dst = (q < a.g.row[u + 1] && a.g.col[q] == x) ? q : -1;
+                  if (dst < 0) atomicOr(a.status + ST_BADGRAPH, 1ull);
+                }
+              } else if (lane == 0) {
+                const unsigned long long q = atomicAdd(a.pair_count, 1ull);
+                if (a.pair_keys) {
+                  if ((int64_t)q < a.pair_cap) {
+                    a.pair_keys[q] = ((unsigned long long)(uint32_t)u << 32) | (uint32_t)x;
+                    dst = (int64_t)q;
+                  } else {
+                    atomicOr(a.status + ST_PAIRCAP, 1ull);
+                  }
+                }
+              }
+              dst = __shfl_sync(0xffffffffu, dst, 0);
+              if (dst >= 0) {
+                u64 *o = a.out_mode == 2 ? a.out + dst * a.R_out : a.pair_rows + dst * a.R_out;
+                for (int t = lane; t < a.R_out; t += 32) o[t] = orow[t];
+              }
+              for (int t = lane; t < a.R_out; t += 32) orow[t] = 0ull;
+            }
+            __syncwarp();
+          }
+        }
+        mine = warp_sum_ck(mine, ovf);
+        if (lane == 0 && mine) {
+          unsigned long long old = atomicAdd(&s_total, mine);
+          if (old + mine < old) ovf |= 1u;
+        }
+      }
+      __syncthreads();
+      // ---- clear the rows and stamps this source touched (scratch returns to zero) ----
+      for (int hf = 0; hf < 2; hf++)
+        for (int j = 1; j <= mat[hf]; j++) {
+          const int cnt = s_cnt[hf * kMaxLevels + j];
+          const int rs = sc.rstride[hf][j], ps = sc.pstride[hf][j];
+          for (int i = tid; i < cnt; i += kCtaThreads) {
+            int32_t w = P.list[hf][j][i];
+            P.list[hf][j][i] = 0;
+            u64 *r = P.rows[hf][j] + (int64_t)w * rs;
+            for (int t = 0; t < rs; t++) r[t] = 0;
+            if (ps) {
+              u64 *q = P.pre[hf][j] + (int64_t)w * ps;
+              for (int t = 0; t < ps; t++) q[t] = 0;
+            }
+            P.stamp[w] = 0;
+          }
+        }
+      for (int i = tid; i < s_cnt[2 * kMaxLevels]; i += kCtaThreads) {
+        P.stamp[P.xlist[i]] = 0;
+        P.xlist[i] = 0;
+      }
+      __syncthreads();
+    }
+    if (a.out_mode == 1 && wrote) {
+      // u's row of the non-root block's table (only this CTA writes it)
+      for (int i = tid; i < a.R_out; i += kCtaThreads) {
+        a.out[(int64_t)u * a.R_out + i] = orow[i];
+        orow[i] = 0;
       }
     }
     if (ovf) atomicOr(&s_ovf, 1u);
@@ -543,7 +644,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch
 static CycleScratch plan_scratch(const CycleArgs &a, int slots) {
   CycleScratch sc;
   int L = a.L, k = a.k;
-  int rp = L / 2, rm = L - L / 2;
+  int rp = a.split ? a.split : L / 2, rm = L - rp;
   bool plain = true;
   for (int i = 0; i < L; i++) plain = plain && !a.N[i].p && !a.Efw[i].p && !a.Ebw[i].p;
   sc.shared_chain = plain;
@@ -595,12 +696,24 @@ size_t cycle_scratch_bytes(const CycleArgs &a, int slots) { return plan_scratch(
 
 int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   if (a_in.L < 4 || a_in.L > kMaxCycle) return CC_ERR_UNSUPPORTED;
+  // a split of one (P+ the single edge u -> x) needs the whole row of x: no vertex order
+  if (a_in.split < 0 || a_in.split >= a_in.L || (a_in.split == 1 && !a_in.no_order)) return CC_ERR_INVALID_ARG;
+  {
+    const int rp = a_in.split ? a_in.split : a_in.L / 2;
+    if (rp > kMaxLevels || a_in.L - rp > kMaxLevels) return CC_ERR_UNSUPPORTED;
+  }
+  if (a_in.out_mode < 0 || a_in.out_mode > 3 || (a_in.out_mode && !a_in.no_order) ||
+      (a_in.out_mode == 2 && a_in.split != 1) || (a_in.out_mode == 3 && !a_in.pair_count))
+    return CC_ERR_INVALID_ARG;
   CycleArgs a = a_in;
+  bool pair_edges = false;
+  for (int i = 0; i < a.L; i++) pair_edges = pair_edges || a.Efw[i].gi >= 0 || a.Ebw[i].gi >= 0;
   // sources of degree >= heavy_degree go to the grouped heavy path
   const int64_t n = a.g.n;
   int hd = c.heavy_degree >= 0 ? c.heavy_degree : (c.cur_tuned_heavy >= 0 ? c.cur_tuned_heavy : 256);
-  // structural counting and the PS procedure run on the per-CTA path only
-  if (a.count_units || a.no_order) hd = 1 << 30;
+  // structural counting, the PS procedure, non-root blocks and pair-keyed
+  // tables run on the per-CTA path only
+  if (a.count_units || a.no_order || a.out_mode || pair_edges) hd = 1 << 30;
   int64_t lo = 0, hi = n;
   while (lo < hi) {
     int64_t mid = (lo + hi) / 2;
@@ -643,7 +756,9 @@ int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   }
   if (cudaMemsetAsync(counter, 0, sizeof(int), c.stream) != cudaSuccess) return CC_ERR_CUDA;
   sc.epoch = 0;
-  size_t smem = (size_t)kWarps * 2 * sc.acc_stride * sizeof(u64) + (a.out ? (size_t)a.R_out * sizeof(u64) : 0);
+  const size_t o_rows = a.out_mode == 0 ? 0 : (a.out_mode == 1 ? (size_t)a.R_out : (size_t)kWarps * a.R_out);
+  size_t smem = (size_t)kWarps * 2 * sc.acc_stride * sizeof(u64) + o_rows * sizeof(u64);
+  if (smem > 200 * 1024) return CC_ERR_UNSUPPORTED;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   timing_begin(c, "cycle_closure");
   k_cycle<<<slots, kCtaThreads, smem, c.stream>>>(a, sc, counter);

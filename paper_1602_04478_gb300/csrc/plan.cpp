@@ -158,6 +158,19 @@ void apply(QS &s, const Cand &x, std::vector<Stage> &st, bool is_root) {
   }
   g.sq_mask = sq;
   g.s = popc(sq);
+  if (!x.leaf && x.nb == 2 && !is_root) {
+    // Case 2: the table is keyed by data edges only when the boundary nodes
+    // are joined by a cycle edge whose images are data edges
+    int i0 = 0, i1 = 0;
+    for (int i = 0; i < x.L; i++) {
+      if (x.nodes[i] == x.bd[0]) i0 = i;
+      if (x.nodes[i] == x.bd[1]) i1 = i;
+    }
+    int e = -1;
+    if ((i0 + 1) % x.L == i1) e = i0;
+    else if ((i1 + 1) % x.L == i0) e = i1;
+    g.pair_out = e < 0 || (g.edge_child[e] >= 0 && st[g.edge_child[e]].pair_out);
+  }
   if (x.leaf) g.kind = ST_LEAF;
   else if (x.L == 3) g.kind = ST_TRI;
   else g.kind = is_root ? (int)ST_CYCLE_ROOT : (int)ST_CYCLE_NONROOT;
@@ -297,8 +310,22 @@ double join_cost(const std::vector<Stage> &st, int k) {
 Score score_of(const std::vector<Stage> &st, int k = 0, bool paper_only = false) {
   Score sc{0, 0, 0, 0.0, 0, 0, (int)st.size(), paper_only};
   for (auto &g : st) {
-    // non-root cycles of length >= 4: one boundary node (Case 1) only
-    if (g.kind == ST_CYCLE_NONROOT && (g.nb != 1 || g.L > kMaxCycle)) sc.unsupported = 1;
+    if (g.kind == ST_CYCLE_NONROOT && g.L > kMaxCycle) sc.unsupported = 1;
+    if (g.kind == ST_CYCLE_NONROOT && g.nb == 2) {
+      // cut at the boundary nodes: the longer half must fit the kernel's levels
+      int i0 = 0, i1 = 0;
+      for (int i = 0; i < g.L; i++) {
+        if (g.nodes[i] == g.bd[0]) i0 = i;
+        if (g.nodes[i] == g.bd[1]) i1 = i;
+      }
+      const int d = (i1 - i0 + g.L) % g.L;
+      if (g.L - std::min(d, g.L - d) > kMaxHalf) sc.unsupported = 1;
+    }
+    // pair-keyed tables: produced and read by the cycle kernel only
+    int ne_g = g.kind == ST_LEAF ? 1 : (g.kind == ST_ROOT_NODE ? 0 : g.L), pair_edges = 0;
+    for (int i = 0; i < ne_g; i++) pair_edges += edge_pair_keyed(st, g, i);
+    if ((g.kind == ST_TRI || g.kind == ST_LEAF) && (pair_edges || g.pair_out)) sc.unsupported = 1;
+    if (pair_edges > kMaxPairGraphs) sc.unsupported = 1;
     if (g.kind == ST_CYCLE_NONROOT) sc.nonroot_long++;
     if (g.kind == ST_CYCLE_ROOT && g.L > kMaxCycle) sc.unsupported = 1;
     if (g.kind == ST_TRI || g.kind == ST_CYCLE_ROOT || g.kind == ST_CYCLE_NONROOT)

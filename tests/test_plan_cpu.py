@@ -58,11 +58,10 @@ def test_satellite_explicit_order_reproduces_paper_tree():
     edges, expect = _read_satellite()
     # B1 = 5-cycle a..e, B2 = leaf (f,h), B3 = 4-cycle (a,f,g,c), B4 = triangle (i,j,k)
     seq = [5, 0, 1, 2, 3, 4, 0, 5, 7, 4, 0, 5, 6, 2, 3, 8, 9, 10]
-    with pytest.raises(P.CCError) as ei:
-        P.cc_plan_inspect(11, edges, seq)
-    # non-root cycles longer than a triangle have no kernel yet
-    assert P.ERRORS[ei.value.code] == "CC_ERR_UNSUPPORTED"
-    blocks, _ = _inspect_anyway(11, edges, seq)
+    # B1's boundary (a, c) is not an edge: its table is pair-keyed, read by
+    # the 4-cycle B3 only, whose own boundary (f, g) is a data edge
+    assert P.cc_plan_supported(11, edges, seq) == 1
+    blocks, _ = P.cc_plan_inspect(11, edges, seq)
     names = {}
     for i, (blk, (name, kind, nodes, bd, kids)) in enumerate(zip(blocks, expect)):
         names[name] = i
@@ -139,3 +138,38 @@ def test_tree_enumeration_and_ranking():
         blocks, _ = P.cc_plan_inspect(k, e)
         again, _ = P.cc_plan_inspect(k, e, lib[0]["seq"]) if lib[0]["seq"] else (blocks, 0)
         assert blocks == again, name
+
+
+def test_shapes_cover_both_cut_orientations():
+    """The Case-2 parity queries' trees include Case-2 blocks whose second boundary node lies
+    within half the cycle of the first in the cycle's own order and beyond it
+    (the kernel then walks the cycle the other way), adjacent pairs (a cut of
+    one edge) and non-adjacent ones."""
+    from test_gpu_case2 import QUERIES as CASE2, _case2_blocks
+    seen = set()
+    for k, e in CASE2.values():
+        for t in P.cc_plan_enumerate(k, e):
+            if t["supported"]:
+                for L, d in _case2_blocks(P, k, e, t["seq"]):
+                    seen.add(("adjacent" if d in (1, L - 1) else "apart", d > L // 2))
+    assert seen >= {("adjacent", False), ("apart", False), ("apart", True)}
+
+
+def test_pair_keyed_tables_are_read_by_cycles_only():
+    """A Case-2 table keyed by pairs that are not data edges is produced and
+    read by the cycle kernel only: a tree whose triangle reads one is not run."""
+    k, e = 6, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (0, 5), (5, 2)]
+    seen = {}
+    for t in P.cc_plan_enumerate(k, e):
+        blocks, _ = P.cc_plan_inspect(k, e, t["seq"], allow_unsupported=True)
+        seen[(len(blocks[0]["nodes"]), blocks[-1]["kind"])] = t["supported"]
+    # the square (0,1,2,5) cut off leaves a root 4-cycle; either 5-cycle, a root triangle
+    assert seen == {(4, "root_cycle"): True, (5, "triangle"): False}
+    # K_{2,3}: every tree ends in a triangle over the pair (0, 1)
+    k23 = [(0, 2), (2, 1), (0, 3), (3, 1), (0, 4), (4, 1)]
+    assert not any(t["supported"] for t in P.cc_plan_enumerate(5, k23))
+    # a 7-cycle whose boundary nodes are adjacent: the long side has 6 edges
+    c7 = [(i, (i + 1) % 7) for i in range(7)] + [(0, 7), (7, 1)]
+    sup = {tuple(len(b["nodes"]) for b in P.cc_plan_inspect(8, c7, t["seq"], allow_unsupported=True)[0]):
+           t["supported"] for t in P.cc_plan_enumerate(8, c7)}
+    assert sup[(7, 3)] is False and sup[(3, 7)] is True
