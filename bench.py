@@ -607,6 +607,84 @@ def run_plan_eval(args):
     return 0
 
 
+CASE2_QUERIES = {
+    # a square and a triangle on one edge (Case-2 square, or Case-2 triangle)
+    "house": (5, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (4, 1)]),
+    # a 5-cycle and a path of two edges between its nodes 0 and 2
+    "theta_5_2": (6, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (0, 5), (5, 2)]),
+    # a 5-cycle and a square on one edge
+    "pentagon_house": (7, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (0, 5), (5, 6), (6, 1)]),
+    # paths of 3, 3 and 3 edges between two nodes
+    "theta_333": (8, [(0, 2), (2, 3), (3, 1), (0, 4), (4, 5), (5, 1), (0, 6), (6, 7), (7, 1)]),
+}
+CASE2_GRAPHS = {
+    "erdos_renyi n=1e5 m=4e5": ("erdos_renyi", 100_000, 400_000, 41),
+    "chung_lu n=2e4 d=8 g=2.1": ("chung_lu", 20_000, 8, 2.1, 42),
+}
+
+
+def run_case2(args):
+    """Case-2 blocks of length >= 4 (two boundary nodes): one colouring of
+    each supported tree of each query, with the library's stage timings
+    (the pair-list count and append launches and the pair-graph build are
+    inside the non-root cycle stage), and the satellite query of the paper's
+    worked decomposition on the smaller graph."""
+    import torch
+
+    import graphgen as gg
+    import paper_1602_04478_gb300 as P
+
+    queries = dict(CASE2_QUERIES)
+    # the Satellite query of the worked decomposition (Section 4.1): 5-cycle
+    # a..e, f on a and g on c, leaf h on f, triangle i, j, k on i with i on f, g
+    queries["satellite"] = (11, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (0, 5), (5, 6), (6, 2), (5, 7), (5, 8),
+                                 (6, 8), (8, 9), (9, 10), (10, 8)])
+    ctx = P.Context(0)
+    stream = ctx.stream
+    P.cc_set_coloring_seed(ctx.h, 9)
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), out
+
+    rows = []
+    for gname, spec in CASE2_GRAPHS.items():
+        g = getattr(gg, spec[0])(*spec[1:])
+        gid = ctx.load_graph(g)
+        for qname, (k, e) in queries.items():
+            if qname == "satellite" and not gname.startswith("chung_lu"):
+                continue
+            for t in P.cc_plan_enumerate(k, e):
+                if not t["supported"]:
+                    continue
+                blocks, _ = P.cc_plan_inspect(k, e, t["seq"] or None)
+                shape = " ".join(f"{b['kind']}{len(b['nodes'])}/{len(b['boundary'])}" for b in blocks)
+                qid = ctx.set_query(k, e)
+                if t["seq"]:
+                    P.cc_set_decomposition(ctx.h, qid, t["seq"])
+                ctx.count(gid, qid, 1, 1, allow_overflow=True)  # warm-up
+                P.cc_reset_timing(ctx.h)
+                P.cc_set_timing(ctx.h, True)
+                ms, (col, _, _) = timed(lambda: ctx.count(gid, qid, 0, 1, allow_overflow=True))
+                stages = P.cc_get_timing(ctx.h)
+                P.cc_set_timing(ctx.h, False)
+                row = {"graph": gname, "query": qname, "tree": shape, "default": t["default"],
+                       "ms_per_colouring": ms, "count": int(col[0]),
+                       "stage_ms": {name: round(v[0], 3) for name, v in stages.items()}}
+                rows.append(row)
+                print(json.dumps({"partial": True, **row}), flush=True)
+        ctx.free_graph(gid)
+    print(json.dumps({"impl": "ours", "mode": "case2", "rows": rows}), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_profile_case(args):
     """Count QUERY (comma-separated list) for `--profile-reps` colourings on a
     Chung-Lu graph of the benchmark's shape (n = --profile-n, mean degree
@@ -672,6 +750,7 @@ def main():
     ap.add_argument("--precision-trials", type=int, default=50)
     ap.add_argument("--ps-compare", action="store_true", help="DB against PS improvement factors")
     ap.add_argument("--plan-eval", action="store_true", help="plan heuristic against the measured best tree")
+    ap.add_argument("--case2", action="store_true", help="Case-2 blocks of length >= 4 (two boundary nodes)")
     args = ap.parse_args()
     if args.rmat_pendants:
         return run_rmat_pendants(args)
@@ -681,6 +760,8 @@ def main():
         return run_ps_compare(args)
     if args.plan_eval:
         return run_plan_eval(args)
+    if args.case2:
+        return run_case2(args)
     if args.profile_case:
         return run_profile_case(args)
     if args.impl == "reference":

@@ -37,6 +37,11 @@ EXTRA = {
     "K23": (5, [(0, 2), (2, 1), (1, 3), (3, 0), (0, 4), (4, 1)]),
     "C6_2pendants_adj": (8, [(i, (i + 1) % 6) for i in range(6)] + [(0, 6), (1, 7)]),
     "C6_2pendants_same": (8, [(i, (i + 1) % 6) for i in range(6)] + [(0, 6), (0, 7)]),
+    # theta graphs: paths between two nodes, so that every tree has a Case-2
+    # block of length >= 4 whose boundary nodes are not adjacent
+    "theta_5_2": (6, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (0, 5), (5, 2)]),
+    "theta_332": (7, [(0, 2), (2, 3), (3, 1), (0, 4), (4, 5), (5, 1), (0, 6), (6, 1)]),
+    "theta_2233": (8, [(0, 1), (1, 2), (0, 5), (5, 2), (0, 4), (4, 3), (3, 2), (0, 6), (6, 7), (7, 2)]),
 }
 
 
