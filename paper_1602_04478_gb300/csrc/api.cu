@@ -356,6 +356,55 @@ int run_case2(Ctx &c, DevGraph &g, const GraphView &gv, const Lut &lut, const ui
   return rc;
 }
 
+bool pair_edges(const Plan &p, const Stage &st) {
+  const int ne = st.kind == ST_LEAF ? 1 : (st.kind == ST_ROOT_NODE ? 0 : st.L);
+  for (int j = 0; j < ne; j++)
+    if (edge_pair_keyed(p.stages, st, j)) return true;
+  return false;
+}
+
+// A triangle with no or one boundary node that reads a pair-keyed table:
+// the cycle kernel with L = 3 and no vertex order (P+ the edge a_0 a_1, P-
+// the path a_0 a_2 a_1), rotated so the boundary node is a_0.  Root: every
+// colourful match once, by a_0's image; one boundary node: the unary table.
+int run_triangle_on_cycle(Ctx &c, const GraphView &gv, const Lut &lut, const uint8_t *colors, int k,
+                          const Stage &st, std::vector<Table> &T, size_t i, u64 *status, bool count_units) {
+  int p0 = 0;
+  if (st.nb == 1)
+    while (p0 < 3 && st.nodes[p0] != st.bd[0]) p0++;
+  if (p0 == 3) return CC_ERR_INVALID_ARG;
+  CycleArgs a;
+  a.g = gv;
+  a.colors = colors;
+  a.k = k;
+  a.lut = lut;
+  a.L = 3;
+  for (int j = 0; j < 3; j++) {
+    const int o = (j + p0) % 3;
+    a.N[j] = tab_u(T, st.node_child[o]);
+    a.Efw[j] = tab_e(T, st.edge_child[o], !st.edge_fwd[o]);
+    a.Ebw[j] = tab_e(T, st.edge_child[o], st.edge_fwd[o]);
+  }
+  a.no_order = true;
+  a.n_h = 1;
+  a.hs[0] = 0;
+  a.multiplier = 1;
+  a.per_vertex = nullptr;
+  a.status = status;
+  a.count_units = count_units;
+  if (st.nb == 1) {
+    a.out_mode = 1;
+    a.out = T[i].p;
+    a.R_out = T[i].R;
+    a.s_out = st.s;
+  }
+  int rc = bind_pairs(a, T);
+  if (rc != CC_OK) return rc;
+  rc = launch_cycle(c, a);
+  if (rc != CC_OK) c.scratch_dirty = c.hv_dirty = true;
+  return rc;
+}
+
 // Issue one colouring pass of the plan on the context's stream: status words
 // zeroed, colours, every block bottom-up into its table, the root into
 // status[ST_COUNT] (and d_per_vertex, rank order, when given).  No host
@@ -408,6 +457,16 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
       w.bytes = 8.0 * ((a.E.p || a.B.p) ? w.units : 0.0) + 4.0 * (double)g.nnz +
                 8.0 * (double)g.n * ((a.A.p ? a.A.R : 0) + R);
       rc = launch_leaf(c, a);
+    } else if (st.kind == ST_TRI && (st.pair_out || pair_edges(p, st))) {
+      // a triangle that reads (or writes) a pair-keyed table runs on the
+      // cycle kernel without vertex order, cut at a_0 and a_1
+      if (st.nb == 2) {
+        rc = run_case2(c, g, gv, lut, B.colors, k, st, T, i, status, count_units);
+      } else if (is_root && d_per_vertex) {
+        rc = CC_ERR_UNSUPPORTED;  // the count would split by a_0's image, not by the highest vertex
+      } else {
+        rc = run_triangle_on_cycle(c, gv, lut, B.colors, k, st, T, i, status, count_units);
+      }
     } else if (st.kind == ST_TRI) {
       TriArgs a;
       a.g = gv;
@@ -418,7 +477,7 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
         a.N[j] = tab_u(T, st.node_child[j]);
         a.E[j] = tab_e(T, st.edge_child[j], !st.edge_fwd[j]);
       }
-      if (any_pair(a.E, 3) || st.pair_out) { rc = CC_ERR_UNSUPPORTED; break; }
+      if (any_pair(a.E, 3) || st.pair_out) { rc = CC_ERR_INVALID_ARG; break; }
       a.nb = st.nb;
       for (int b = 0; b < st.nb; b++)
         for (int j = 0; j < 3; j++)

@@ -695,7 +695,8 @@ static CycleScratch plan_scratch(const CycleArgs &a, int slots) {
 size_t cycle_scratch_bytes(const CycleArgs &a, int slots) { return plan_scratch(a, slots).slot_bytes * (size_t)slots; }
 
 int launch_cycle(Ctx &c, const CycleArgs &a_in) {
-  if (a_in.L < 4 || a_in.L > kMaxCycle) return CC_ERR_UNSUPPORTED;
+  // triangles come here only without vertex order (pair-keyed tables)
+  if (a_in.L < 3 || (a_in.L == 3 && !a_in.no_order) || a_in.L > kMaxCycle) return CC_ERR_UNSUPPORTED;
   // a split of one (P+ the single edge u -> x) needs the whole row of x: no vertex order
   if (a_in.split < 0 || a_in.split >= a_in.L || (a_in.split == 1 && !a_in.no_order)) return CC_ERR_INVALID_ARG;
   {

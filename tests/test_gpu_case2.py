@@ -29,12 +29,19 @@ QUERIES = {
     # paths of 2, 2, 3 and 3 edges between nodes 0 and 2: a square whose
     # boundary edge is itself a pair-keyed edge
     "theta_2233": (8, [(0, 1), (1, 2), (0, 5), (5, 2), (0, 4), (4, 3), (3, 2), (0, 6), (6, 7), (7, 2)]),
+    # K_{2,3}: every tree ends in a root triangle over a pair-keyed edge
+    "K23": (5, [(0, 2), (2, 1), (1, 3), (3, 0), (0, 4), (4, 1)]),
+    # K_{2,3} and a triangle on node 1: a triangle with one boundary node reads a pair
+    "K23_tail": (7, [(0, 2), (2, 1), (1, 3), (3, 0), (0, 4), (4, 1), (1, 5), (5, 6), (6, 1)]),
+    # K_{2,4}: a triangle with both boundary nodes on a pair-keyed edge writes a pair list
+    "K24": (6, [(0, 1), (1, 2), (0, 3), (3, 2), (0, 4), (4, 2), (0, 5), (5, 2)]),
 }
 GRAPHS = {"er60": lambda: gg.erdos_renyi(60, 300, 1), "cl1000": lambda: gg.chung_lu(1000, 6, 2.1, 3)}
 
 
 def _case2_blocks(P, k, e, seq):
-    """(L, distance from the first boundary node to the second) per Case-2 cycle block."""
+    """(L, distance from the first boundary node to the second) per Case-2
+    block of length >= 4."""
     blocks, _ = P.cc_plan_inspect(k, e, seq or None)
     out = []
     for b in blocks:
@@ -81,7 +88,7 @@ def _every_tree(cc, g, k, e, trials=2, seed=10):
 def test_every_tree_matches_oracle(cc, gname, qname):
     k, e = QUERIES[qname]
     shapes, want = _every_tree(cc, GRAPHS[gname](), k, e)
-    assert shapes  # at least one tree takes a Case-2 cycle of length >= 4
+    assert shapes  # at least one tree takes a Case-2 cycle
     assert any(w > 0 for w in want)
 
 

@@ -436,12 +436,11 @@ def test_k_range_error(cc):
 
 
 def test_unsupported_block_reported(cc):
-    # K_{2,3}: every 4-cycle block has two boundary nodes that are not
-    # adjacent (Case 2 with a non-adjacent pair), which has no kernel
+    # a 9-cycle: longer than the cycle kernel's 8 nodes, and its only tree
     import paper_1602_04478_gb300 as P
-    e = [(0, 2), (2, 1), (1, 3), (3, 0), (0, 4), (4, 1)]
+    e = [(i, (i + 1) % 9) for i in range(9)]
     with pytest.raises(P.CCError) as ei:
-        cc.set_query(5, e)
+        cc.set_query(9, e)
     assert P.ERRORS[ei.value.code] == "CC_ERR_UNSUPPORTED"
 
 

@@ -157,17 +157,26 @@ def test_shapes_cover_both_cut_orientations():
 
 def test_pair_keyed_tables_are_read_by_cycles_only():
     """A Case-2 table keyed by pairs that are not data edges is produced and
-    read by the cycle kernel only: a tree whose triangle reads one is not run."""
+    read by the cycle kernel only (a triangle that reads one runs there too);
+    a leaf block that reads one is not run."""
     k, e = 6, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (0, 5), (5, 2)]
     seen = {}
     for t in P.cc_plan_enumerate(k, e):
         blocks, _ = P.cc_plan_inspect(k, e, t["seq"], allow_unsupported=True)
         seen[(len(blocks[0]["nodes"]), blocks[-1]["kind"])] = t["supported"]
     # the square (0,1,2,5) cut off leaves a root 4-cycle; either 5-cycle, a root triangle
-    assert seen == {(4, "root_cycle"): True, (5, "triangle"): False}
+    assert seen == {(4, "root_cycle"): True, (5, "triangle"): True}
     # K_{2,3}: every tree ends in a triangle over the pair (0, 1)
     k23 = [(0, 2), (2, 1), (0, 3), (3, 1), (0, 4), (4, 1)]
-    assert not any(t["supported"] for t in P.cc_plan_enumerate(5, k23))
+    assert all(t["supported"] for t in P.cc_plan_enumerate(5, k23))
+    # a square with pendants on opposite nodes: cut off first, the square
+    # leaves the pair (0, 2) as a leaf edge
+    sq = [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (2, 5)]
+    sup = {}
+    for t in P.cc_plan_enumerate(6, sq):
+        blocks, _ = P.cc_plan_inspect(6, sq, t["seq"], allow_unsupported=True)
+        sup.setdefault(blocks[0]["kind"], set()).add(t["supported"])
+    assert sup["cycle"] == {False} and sup["leaf"] == {True}
     # a 7-cycle whose boundary nodes are adjacent: the long side has 6 edges
     c7 = [(i, (i + 1) % 7) for i in range(7)] + [(0, 7), (7, 1)]
     sup = {tuple(len(b["nodes"]) for b in P.cc_plan_inspect(8, c7, t["seq"], allow_unsupported=True)[0]):
