@@ -155,13 +155,13 @@ int cc_plan_inspect(int k, int n_edges, const int32_t *edges, const int32_t *blo
 /* Host-only: 1 if the kernels run the plan cc_plan_inspect describes for the
  * same arguments, 0 if not (cc_set_query / cc_set_decomposition would answer
  * CC_ERR_UNSUPPORTED), or a CC_ERR_ code for an invalid query or order.  Not
- * run: a cycle longer than 8; a leaf block that reads a Case-2 table keyed
- * by pairs that need not be data edges (Section 4.1, Case 2: boundary nodes
- * not adjacent in their cycle); a cycle reading more than four such tables;
- * a Case-2 cycle whose longer side between its boundary nodes has more than
- * 5 edges.  (Cycles and triangles that read or write such tables run on the
- * general cycle kernel; a root triangle that reads one has no per-vertex
- * split: cc_count_per_vertex answers CC_ERR_UNSUPPORTED for it.) */
+ * run: a cycle longer than 8; a cycle reading more than four Case-2 tables
+ * keyed by pairs that need not be data edges (Section 4.1, Case 2: boundary
+ * nodes not adjacent in their cycle); a Case-2 cycle whose longer side
+ * between its boundary nodes has more than 5 edges.  (Cycles and triangles
+ * that read or write such tables run on the general cycle kernel, a leaf
+ * over one walks its pair graph; a root triangle that reads one has no
+ * per-vertex split: cc_count_per_vertex answers CC_ERR_UNSUPPORTED for it.) */
 int cc_plan_supported(int k, int n_edges, const int32_t *edges, const int32_t *block_seq, int seq_len);
 
 /* Host-only: every decomposition tree of a query (Section 5.3), one record

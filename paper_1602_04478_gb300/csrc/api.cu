@@ -441,7 +441,21 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
       a.A = tab_u(T, st.node_child[0]);
       a.B = tab_u(T, st.node_child[1]);
       a.E = tab_e(T, st.edge_child[0], !st.edge_fwd[0]);
-      if (a.E.gi >= 0) { rc = CC_ERR_UNSUPPORTED; break; }  // pair-keyed: the cycle kernel's only
+      u64 *dense = nullptr;
+      size_t dense_bytes = 0;
+      if (a.E.gi >= 0) {
+        // a leaf over a pair-keyed edge walks the pair graph, with the rows
+        // laid out by its positions like an edge-keyed table
+        const PairGraph &pg = T[a.E.gi].pg;
+        dense_bytes = (size_t)std::max<int64_t>(pg.nnz, 1) * pg.R * 8;
+        dense = (u64 *)dev_alloc(c, dense_bytes);
+        if (!dense) { rc = CC_ERR_OOM; break; }
+        if ((rc = pair_rows_by_position(c, pg, dense)) != CC_OK) { dev_free(c, dense, dense_bytes); break; }
+        a.g = pair_view(pg);
+        a.E.p = dense;
+        a.E.ridx = nullptr;
+        a.E.gi = -1;
+      }
       int sE = a.E.p ? a.E.s : 2, sB = a.B.p ? a.B.s : 1, sA = a.A.p ? a.A.s : 1;
       a.sY = sE + sB - 1;
       a.RY = (int)binom(k - 1, a.sY - 1);
@@ -457,6 +471,7 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
       w.bytes = 8.0 * ((a.E.p || a.B.p) ? w.units : 0.0) + 4.0 * (double)g.nnz +
                 8.0 * (double)g.n * ((a.A.p ? a.A.R : 0) + R);
       rc = launch_leaf(c, a);
+      dev_free(c, dense, dense_bytes);  // stream-ordered after the join
     } else if (st.kind == ST_TRI && (st.pair_out || pair_edges(p, st))) {
       // a triangle that reads (or writes) a pair-keyed table runs on the
       // cycle kernel without vertex order, cut at a_0 and a_1

@@ -136,6 +136,8 @@ struct PairGraph {
 };
 int pair_graph_build(Ctx &c, int64_t n, const unsigned long long *keys, int64_t n_pairs, PairGraph &pg);
 void pair_graph_free(Ctx &c, PairGraph &pg);
+// dense[q][R] = the row of position q (zero where none), for a leaf block's join
+int pair_rows_by_position(Ctx &c, const PairGraph &pg, u64 *dense);
 int run_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank, int B);
 bool plain_cycle_eligible(const CycleArgs &a);
 int run_plain_heavy(Ctx &c, const CycleArgs &a, int32_t first_rank);

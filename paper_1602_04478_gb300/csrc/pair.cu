@@ -82,6 +82,16 @@ __global__ void k_pair_rev(const unsigned long long *ukeys, const int64_t *row, 
   }
 }
 
+// rows by position (the reverse-only positions zero) for kernels that index
+// an edge-keyed table by CSR position
+__global__ void k_pair_dense(const int64_t *ridx, const u64 *rows, int64_t nnz, int R, u64 *dense) {
+  const int64_t total = nnz * R;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = i / R, r = ridx[q];
+    dense[i] = r < 0 ? 0ull : rows[r * R + (i - q * R)];
+  }
+}
+
 int grid_for(int64_t m) { return (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 152 * 16)); }
 
 }  // namespace
@@ -175,6 +185,13 @@ int pair_graph_build(Ctx &c, int64_t n, const unsigned long long *keys, int64_t 
   dev_free(c, tmp, tb);
   dev_free(c, ukeys, (size_t)std::max<int64_t>(pg.nnz, 1) * 8);
   return rc;
+}
+
+int pair_rows_by_position(Ctx &c, const PairGraph &pg, u64 *dense) {
+  if (pg.nnz == 0) return CC_OK;
+  k_pair_dense<<<grid_for(pg.nnz * pg.R), 256, 0, c.stream>>>(pg.ridx, pg.rows, pg.nnz, pg.R, dense);
+  c.kernels++;
+  return cudaGetLastError() == cudaSuccess ? CC_OK : CC_ERR_CUDA;
 }
 
 }  // namespace cc

@@ -324,7 +324,6 @@ Score score_of(const std::vector<Stage> &st, int k = 0, bool paper_only = false)
     // pair-keyed tables: produced and read by the cycle kernel only
     int ne_g = g.kind == ST_LEAF ? 1 : (g.kind == ST_ROOT_NODE ? 0 : g.L), pair_edges = 0;
     for (int i = 0; i < ne_g; i++) pair_edges += edge_pair_keyed(st, g, i);
-    if (g.kind == ST_LEAF && pair_edges) sc.unsupported = 1;
     if (pair_edges > kMaxPairGraphs) sc.unsupported = 1;
     if (g.kind == ST_CYCLE_NONROOT) sc.nonroot_long++;
     if (g.kind == ST_CYCLE_ROOT && g.L > kMaxCycle) sc.unsupported = 1;

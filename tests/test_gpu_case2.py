@@ -35,6 +35,9 @@ QUERIES = {
     "K23_tail": (7, [(0, 2), (2, 1), (1, 3), (3, 0), (0, 4), (4, 1), (1, 5), (5, 6), (6, 1)]),
     # K_{2,4}: a triangle with both boundary nodes on a pair-keyed edge writes a pair list
     "K24": (6, [(0, 1), (1, 2), (0, 3), (3, 2), (0, 4), (4, 2), (0, 5), (5, 2)]),
+    # a square with pendants on opposite nodes: cut off first, the square
+    # leaves its pair as a leaf edge (the leaf join walks the pair graph)
+    "square_opposite_pendants": (6, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4), (2, 5)]),
 }
 GRAPHS = {"er60": lambda: gg.erdos_renyi(60, 300, 1), "cl1000": lambda: gg.chung_lu(1000, 6, 2.1, 3)}
 

@@ -155,10 +155,10 @@ def test_shapes_cover_both_cut_orientations():
     assert seen >= {("adjacent", False), ("apart", False), ("apart", True)}
 
 
-def test_pair_keyed_tables_are_read_by_cycles_only():
+def test_support_of_pair_keyed_tables():
     """A Case-2 table keyed by pairs that are not data edges is produced and
-    read by the cycle kernel only (a triangle that reads one runs there too);
-    a leaf block that reads one is not run."""
+    read by the cycle kernel (a triangle that reads one runs there too) and
+    by the leaf join over its pair graph."""
     k, e = 6, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (0, 5), (5, 2)]
     seen = {}
     for t in P.cc_plan_enumerate(k, e):
@@ -176,7 +176,7 @@ def test_pair_keyed_tables_are_read_by_cycles_only():
     for t in P.cc_plan_enumerate(6, sq):
         blocks, _ = P.cc_plan_inspect(6, sq, t["seq"], allow_unsupported=True)
         sup.setdefault(blocks[0]["kind"], set()).add(t["supported"])
-    assert sup["cycle"] == {False} and sup["leaf"] == {True}
+    assert sup["cycle"] == {True} and sup["leaf"] == {True}
     # a 7-cycle whose boundary nodes are adjacent: the long side has 6 edges
     c7 = [(i, (i + 1) % 7) for i in range(7)] + [(0, 7), (7, 1)]
     sup = {tuple(len(b["nodes"]) for b in P.cc_plan_inspect(8, c7, t["seq"], allow_unsupported=True)[0]):
