@@ -706,7 +706,7 @@ def run_profile_case(args):
     out = {"profile_case": args.profile_case, "n": n, "mean_deg": mean, "heavy_degree": args.heavy_degree,
            "budget_gib": args.profile_budget, "queries": {}}
     for name in args.profile_case.split(","):
-        q = ctx.set_query(*gg.query(name))
+        q = ctx.set_query(*(CASE2_QUERIES[name] if name in CASE2_QUERIES else gg.query(name)))
         detail = P.cc_work_detail(ctx.h, gid, q)
         ctx.count(gid, q, 100, 1, allow_overflow=True)  # per-graph structure, outside the captured launches
         cols = [int(ctx.count(gid, q, t, 1, allow_overflow=True)[0][0]) for t in range(args.profile_reps)]

@@ -317,7 +317,10 @@ int run_case2(Ctx &c, DevGraph &g, const GraphView &gv, const Lut &lut, const ui
     if (rc != CC_OK) c.scratch_dirty = c.hv_dirty = true;
     return rc;
   }
-  // pair list: count, size, append, then the pair graph
+  // pair list: append into buffers sized from the previous pass of this
+  // stage on this graph (the entries vary little between colourings); the
+  // launch counts every entry, so one that did not fit is run again into
+  // buffers of the exact size.  The first pass only counts.
   if (T[i].pair) pair_graph_free(c, T[i].pg);
   T[i].pair = false;
   unsigned long long *cnt = (unsigned long long *)dev_alloc(c, 16);
@@ -325,34 +328,59 @@ int run_case2(Ctx &c, DevGraph &g, const GraphView &gv, const Lut &lut, const ui
   unsigned long long *keys = nullptr;
   u64 *rows = nullptr;
   unsigned long long np = 0;
+  int64_t cap = 0;
   const size_t R = (size_t)T[i].R;
+  const auto hint_key = std::make_pair((const void *)&st, (int)i);
+  auto hint = g.pair_hint.find(hint_key);
+  auto alloc_lists = [&](int64_t m) {
+    cap = std::max<int64_t>(m, 1);
+    keys = (unsigned long long *)dev_alloc(c, (size_t)cap * 8);
+    rows = (u64 *)dev_alloc(c, (size_t)cap * R * 8);
+    return keys && rows;
+  };
   do {
     a.out_mode = 3;
     a.pair_count = cnt;
+    if (hint != g.pair_hint.end()) {
+      if (!alloc_lists(hint->second + hint->second / 4 + 1024)) { rc = CC_ERR_OOM; break; }
+      a.pair_keys = keys;
+      a.pair_rows = rows;
+      a.pair_cap = cap;
+    }
     if ((rc = check(cudaMemsetAsync(cnt, 0, 16, c.stream))) != CC_OK) break;
     if ((rc = launch_cycle(c, a)) != CC_OK) break;
     if ((rc = check(cudaMemcpyAsync(&np, cnt, 8, cudaMemcpyDeviceToHost, c.stream))) != CC_OK) break;
     if ((rc = check(cudaStreamSynchronize(c.stream))) != CC_OK) break;
-    keys = (unsigned long long *)dev_alloc(c, (size_t)std::max<unsigned long long>(np, 1) * 8);
-    rows = (u64 *)dev_alloc(c, (size_t)std::max<unsigned long long>(np, 1) * R * 8);
-    if (!keys || !rows) { rc = CC_ERR_OOM; break; }
-    a.pair_keys = keys;
-    a.pair_rows = rows;
-    a.pair_cap = (int64_t)np;
-    a.count_units = false;  // the structural work was counted by the first launch
-    if ((rc = check(cudaMemsetAsync(cnt, 0, 16, c.stream))) != CC_OK) break;
-    if ((rc = launch_cycle(c, a)) != CC_OK) break;
+    if (!keys || (int64_t)np > cap) {
+      // counted only, or outgrown: the exact size, and the launch again
+      cudaStreamSynchronize(c.stream);
+      dev_free(c, keys, (size_t)cap * 8);
+      dev_free(c, rows, (size_t)cap * R * 8);
+      keys = nullptr;
+      rows = nullptr;
+      if (!alloc_lists((int64_t)np)) { rc = CC_ERR_OOM; break; }
+      a.pair_keys = keys;
+      a.pair_rows = rows;
+      a.pair_cap = cap;
+      a.count_units = false;  // the structural work was counted by the first launch
+      // the overflowing launch may have flagged the list's capacity
+      if ((rc = check(cudaMemsetAsync(status + ST_PAIRCAP, 0, 8, c.stream))) != CC_OK) break;
+      if ((rc = check(cudaMemsetAsync(cnt, 0, 16, c.stream))) != CC_OK) break;
+      if ((rc = launch_cycle(c, a)) != CC_OK) break;
+    }
+    g.pair_hint[hint_key] = (int64_t)np;
     T[i].pg.rows = rows;
+    T[i].pg.rows_cap = cap;
     T[i].pg.R = (int)R;
     T[i].pair = true;
-    rows = nullptr;  // owned by the pair graph now
+    rows = nullptr;  // owned by the pair graph now (freed with the pass)
     rc = pair_graph_build(c, g.n, keys, (int64_t)np, T[i].pg);
   } while (false);
   if (rc != CC_OK) c.scratch_dirty = c.hv_dirty = true;
   cudaStreamSynchronize(c.stream);
   dev_free(c, cnt, 16);
-  dev_free(c, keys, (size_t)std::max<unsigned long long>(np, 1) * 8);
-  dev_free(c, rows, (size_t)std::max<unsigned long long>(np, 1) * R * 8);
+  dev_free(c, keys, (size_t)cap * 8);
+  dev_free(c, rows, (size_t)cap * R * 8);
   return rc;
 }
 

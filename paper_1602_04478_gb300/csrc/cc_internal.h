@@ -104,6 +104,9 @@ struct DevGraph {
   int64_t n_tri = 0;
   int32_t *tri_u = nullptr, *tri_v = nullptr, *tri_w = nullptr;
   int64_t *tri_p = nullptr;          // [3][n_tri]
+  // pair lists of Case-2 blocks: entries of the last pass, by (plan, stage) --
+  // the next pass sizes its buffers from it and appends in one launch
+  std::map<std::pair<const void *, int>, int64_t> pair_hint;
 };
 
 // -------------------------------- context --------------------------------

@@ -131,7 +131,8 @@ struct PairGraph {
   int64_t *rev = nullptr;
   int32_t *lo_cnt = nullptr;
   int64_t *ridx = nullptr;
-  u64 *rows = nullptr;  // [n_pairs][R]
+  u64 *rows = nullptr;  // [n_pairs][R] in a buffer of rows_cap rows
+  int64_t rows_cap = 0;
   int R = 0;
 };
 int pair_graph_build(Ctx &c, int64_t n, const unsigned long long *keys, int64_t n_pairs, PairGraph &pg);

@@ -102,12 +102,12 @@ void pair_graph_free(Ctx &c, PairGraph &pg) {
   dev_free(c, pg.rev, (size_t)std::max<int64_t>(pg.nnz, 1) * 8);
   dev_free(c, pg.lo_cnt, (size_t)std::max<int64_t>(pg.n, 1) * 4);
   dev_free(c, pg.ridx, (size_t)std::max<int64_t>(pg.nnz, 1) * 8);
-  dev_free(c, pg.rows, (size_t)std::max<int64_t>(pg.n_pairs, 1) * pg.R * 8);
+  dev_free(c, pg.rows, (size_t)std::max<int64_t>(pg.rows_cap, 1) * pg.R * 8);
   pg = PairGraph();
 }
 
-// keys: the n_pairs distinct appended keys (device).  pg.rows and pg.R are
-// the caller's (the appended rows, kept as they are).  Synchronises.
+// keys: the n_pairs distinct appended keys (device).  pg.rows, rows_cap and
+// R are the caller's (the appended rows, kept as they are).  Synchronises.
 int pair_graph_build(Ctx &c, int64_t n, const unsigned long long *keys, int64_t n_pairs, PairGraph &pg) {
   pg.n = n;
   pg.n_pairs = n_pairs;

@@ -136,3 +136,25 @@ def test_pair_list_plan_in_a_batch(cc):
             assert [int(x) for x in got[0]] == want and st == [0]
     finally:
         cc.free_graph(gid)
+
+
+def test_pair_list_outgrows_the_previous_pass(cc):
+    """The pair list of a pass is sized from the previous pass on the same
+    graph; a colouring with far more pairs than the last one (here after a
+    single-colour colouring with none) runs its append again into buffers of
+    the exact size and still gives the oracle's count."""
+    import numpy as np
+    import paper_1602_04478_gb300 as P
+    k, e = QUERIES["theta_5_2"]
+    g = gg.chung_lu(3000, 8, 2.1, 3)
+    gid = cc.load_graph(g)
+    try:
+        cols = np.stack([np.zeros(g.n, dtype=np.uint8), O.colors(8, 0, g.n, k), O.colors(8, 1, g.n, k)])
+        P.cc_set_colors(cc.h, gid, cols)
+        want = [0] + [O.dp_count(g, k, e, cols[t])[0] for t in (1, 2)]
+        qid = cc.set_query(k, e)
+        got = [int(x) for x in cc.count(gid, qid, 0, 3)[0]]
+        assert got == want and want[1] > 0
+    finally:
+        P.cc_clear_colors(cc.h, gid)
+        cc.free_graph(gid)
