@@ -179,7 +179,11 @@ __global__ void __launch_bounds__(256) k_leaf_join_flat(LeafArgs a) {
 // slot s -- inv[(cx k + cy) RY + s], or -1 when there is none -- and adds it
 // to its own register.  No atomics; a row's entries are read by neighbouring
 // lanes.  With Y rows of at most 16 slots each half-warp takes its own
-// neighbours and the halves are summed at the end.
+// neighbours and the halves are summed at the end.  Neighbour ids and their
+// colours are read 32 at a time (one per lane) and passed round by shuffles,
+// and four neighbours' row entries are loaded before any is added, so each
+// lane has four independent gathers in flight instead of a chain of three
+// dependent loads per neighbour.
 __global__ void __launch_bounds__(256) k_leaf_join_slots(LeafArgs a) {
   extern __shared__ __align__(16) unsigned char slots_smem[];
   int16_t *inv = reinterpret_cast<int16_t *>(slots_smem);
@@ -207,13 +211,24 @@ __global__ void __launch_bounds__(256) k_leaf_join_slots(LeafArgs a) {
     const int deg = (int)(a.g.row[x + 1] - rb);
     const int16_t *ix = inv + (size_t)cx * k * RY;
     u64 acc = 0;
-    if (s < RY) {
-      for (int i = h; i < deg; i += step) {
-        const int32_t y = __ldg(a.g.col + rb + i);
-        if (!cc_in(y, a.g.n, a.status)) continue;
-        const int j = ix[a.colors[y] * RY + s];
-        if (j < 0) continue;
-        acc = add_ck(acc, a.B.p ? __ldg(a.B.p + (int64_t)y * RB + j) : 1ull, ovf);
+    for (int base = 0; base < deg; base += 32) {
+      // this chunk's neighbours and colours, one per lane
+      const int cnt = min(32, deg - base);
+      int32_t yl = lane < cnt ? __ldg(a.g.col + rb + base + lane) : -1;
+      if (yl >= 0 && !cc_in(yl, a.g.n, a.status)) yl = -1;
+      const int cl = yl >= 0 ? (int)a.colors[yl] : 0;
+      for (int t0 = 0; t0 < cnt; t0 += 4 * step) {
+        u64 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int t = t0 + h + q * step;  // the neighbour this lane takes
+          const int32_t y = __shfl_sync(0xffffffffu, yl, t & 31);
+          const int cy = __shfl_sync(0xffffffffu, cl, t & 31);
+          const int j = (t < cnt && s < RY && y >= 0) ? ix[cy * RY + s] : -1;
+          v[q] = j < 0 ? 0ull : (a.B.p ? __ldg(a.B.p + (int64_t)y * RB + j) : 1ull);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc = add_ck(acc, v[q], ovf);
       }
     }
     if (halves) acc = add_ck(acc, __shfl_down_sync(0xffffffffu, acc, 16), ovf);
