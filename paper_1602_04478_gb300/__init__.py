@@ -353,7 +353,7 @@ def cc_work_units(h, gid: int, qid: int) -> float:
     return u.value
 
 
-STAGE_KINDS = {0: "leaf", 1: "triangle", 2: "root_cycle", 3: "root_node"}
+STAGE_KINDS = {0: "leaf", 1: "triangle", 2: "root_cycle", 3: "root_node", 4: "cycle"}
 
 
 def cc_work_detail(h, gid: int, qid: int):

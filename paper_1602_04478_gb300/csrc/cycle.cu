@@ -761,7 +761,8 @@ int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   size_t smem = (size_t)kWarps * 2 * sc.acc_stride * sizeof(u64) + o_rows * sizeof(u64);
   if (smem > 200 * 1024) return CC_ERR_UNSUPPORTED;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  timing_begin(c, "cycle_closure");
+  // timed apart: root closures, Case-1 blocks, Case-2 blocks
+  timing_begin(c, a.out_mode == 0 ? "cycle_closure" : (a.out_mode == 1 ? "cycle_case1" : "cycle_case2"));
   k_cycle<<<slots, kCtaThreads, smem, c.stream>>>(a, sc, counter);
   c.kernels++;
   timing_end(c);

@@ -96,6 +96,8 @@ int grid_for(int64_t m) { return (int)std::max<int64_t>(1, std::min<int64_t>((m 
 
 }  // namespace
 
+int pair_graph_sort(Ctx &c, int64_t n, const unsigned long long *keys, int64_t n_pairs, int64_t m, PairGraph &pg);
+
 void pair_graph_free(Ctx &c, PairGraph &pg) {
   dev_free(c, pg.row, (size_t)(pg.n + 1) * 8);
   dev_free(c, pg.col, (size_t)std::max<int64_t>(pg.nnz, 1) * 4);
@@ -127,6 +129,14 @@ int pair_graph_build(Ctx &c, int64_t n, const unsigned long long *keys, int64_t 
       return CC_ERR_CUDA;
     return CC_OK;
   }
+  timing_begin(c, "pair_graph_build");
+  const int rc_build = pair_graph_sort(c, n, keys, n_pairs, m, pg);
+  timing_end(c);
+  return rc_build;
+}
+
+int pair_graph_sort(Ctx &c, int64_t n, const unsigned long long *keys, int64_t n_pairs, int64_t m, PairGraph &pg) {
+  cudaStream_t st = c.stream;
   size_t tb_sort = 0, tb_scan = 0;
   cub::DeviceRadixSort::SortPairs(nullptr, tb_sort, (unsigned long long *)nullptr, (unsigned long long *)nullptr,
                                   (int64_t *)nullptr, (int64_t *)nullptr, (int)m, 0, 64, st);
