@@ -249,7 +249,13 @@ __device__ __forceinline__ void pull_hop(const CycleArgs &a, const GraphView &gg
              ovf);
 }
 
-__global__ void __launch_bounds__(kCtaThreads) k_cycle(CycleArgs a, CycleScratch sc, int *work_counter) {
+// resident CTAs per SM the register allocation is held to
+#ifndef CC_CYCLE_MIN_BLOCKS
+#define CC_CYCLE_MIN_BLOCKS 2
+#endif
+
+__global__ void __launch_bounds__(kCtaThreads, CC_CYCLE_MIN_BLOCKS)
+    k_cycle(CycleArgs a, CycleScratch sc, int *work_counter) {
   extern __shared__ u64 smem_acc[];
   __shared__ int s_u;
   __shared__ int s_cnt[2 * kMaxLevels + 1];
