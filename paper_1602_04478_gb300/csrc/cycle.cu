@@ -249,13 +249,12 @@ __device__ __forceinline__ void pull_hop(const CycleArgs &a, const GraphView &gg
              ovf);
 }
 
-// resident CTAs per SM the register allocation is held to
-#ifndef CC_CYCLE_MIN_BLOCKS
-#define CC_CYCLE_MIN_BLOCKS 2
-#endif
-
-__global__ void __launch_bounds__(kCtaThreads, CC_CYCLE_MIN_BLOCKS)
-    k_cycle(CycleArgs a, CycleScratch sc, int *work_counter) {
+// MB: resident CTAs per SM the register allocation is held to.  Launches
+// without vertex order (PS, non-root blocks) take 4 (measured: C6 by PS on a
+// 10^5-vertex Chung-Lu graph 9.8 s -> 6.1 s), the DB closures 2 (4 was 4-8%
+// slower on annotated root cycles).
+template <int MB>
+__global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScratch sc, int *work_counter) {
   extern __shared__ u64 smem_acc[];
   __shared__ int s_u;
   __shared__ int s_cnt[2 * kMaxLevels + 1];
@@ -766,10 +765,14 @@ int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   const size_t o_rows = a.out_mode == 0 ? 0 : (a.out_mode == 1 ? (size_t)a.R_out : (size_t)kWarps * a.R_out);
   size_t smem = (size_t)kWarps * 2 * sc.acc_stride * sizeof(u64) + o_rows * sizeof(u64);
   if (smem > 200 * 1024) return CC_ERR_UNSUPPORTED;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_cycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) {
+    cudaFuncSetAttribute(k_cycle<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_cycle<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
   // timed apart: root closures, Case-1 blocks, Case-2 blocks
   timing_begin(c, a.out_mode == 0 ? "cycle_closure" : (a.out_mode == 1 ? "cycle_case1" : "cycle_case2"));
-  k_cycle<<<slots, kCtaThreads, smem, c.stream>>>(a, sc, counter);
+  if (a.no_order) k_cycle<4><<<slots, kCtaThreads, smem, c.stream>>>(a, sc, counter);
+  else k_cycle<2><<<slots, kCtaThreads, smem, c.stream>>>(a, sc, counter);
   c.kernels++;
   timing_end(c);
   // the queue counter returns to zero too: the whole scratch is zero between launches
