@@ -49,16 +49,14 @@ WORKLOAD = {"graph": "chung_lu", "n": 1_000_000, "mean_deg": 16, "gamma": 2.1, "
             "queries": ["C6", "glasses"], "form": "plain", "colourings_per_query_per_step": 1}
 COLOR_SEED = 1
 BATCH_QUERIES = ["C5", "chord_pendant", "glasses"]
-# DRAM bytes (read + written) per colouring of each kernel family on the
-# benchmark graph, estimated from an ncu capture of every launch of those
-# kernels on a small case of the same shape (Chung-Lu n = 2e5, mean 16,
-# gamma 2.1; one C6 and one glasses colouring): the small case's DRAM bytes
-# per algorithmic byte times the full workload's algorithmic bytes
-# (closure 24.48 GB / 13.01 GB, leaf joins 0.1325 / 0.978, triangle list
-# 0.204 / 0.963).  The small case's tables fit in L2, so the leaf-join and
-# triangle ratios are lower bounds.
-TRAFFIC_BYTES = {"cycle_closure": 140.90e9 * 24.48 / 13.01, "leaf_join": 4.887e9 * 0.1325 / 0.978,
-                 "triangle": 8.119e9 * 0.204 / 0.963}
+# DRAM bytes (read + written) per algorithmic byte of each kernel family,
+# from an ncu capture of every launch of those kernels on a small case of the
+# benchmark's shape (Chung-Lu n = 2e5, mean 16, gamma 2.1; one C6 and one
+# glasses colouring): the closure 24.48 GB / 13.01 GB, the leaf joins and
+# the triangle list as set below.  The bench multiplies them by the full
+# workload's algorithmic bytes.  The small case's tables fit in L2, so the
+# leaf-join and triangle ratios are lower bounds.
+TRAFFIC_PER_ALG_BYTE = {"cycle_closure": 24.48 / 13.01, "leaf_join": None, "triangle": None}
 FLUSH_BYTES = 256 << 20
 # CPU baseline: whole colourings on a smaller graph of the benchmark's shape
 CPU_GRAPH = {"graph": "chung_lu", "n": 2_000, "mean_deg": 16, "gamma": 2.1, "seed": 2}
@@ -866,7 +864,8 @@ def main():
         if not names or f_ms <= 0:
             continue
         ach = nbytes / (f_ms / 1e3) / 1e9
-        tr = TRAFFIC_BYTES.get(fam)
+        ratio = TRAFFIC_PER_ALG_BYTE.get(fam)
+        tr = ratio * nbytes if ratio else None
         kernel_rooflines[fam] = {
             "kernels": names, "bound": "hbm", "alg_bytes_per_colouring": nbytes, "ms_per_colouring": f_ms,
             "launches_per_colouring": sum(kern[k][1] for k in names) / args.steps,
