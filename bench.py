@@ -52,11 +52,12 @@ BATCH_QUERIES = ["C5", "chord_pendant", "glasses"]
 # DRAM bytes (read + written) per algorithmic byte of each kernel family,
 # from an ncu capture of every launch of those kernels on a small case of the
 # benchmark's shape (Chung-Lu n = 2e5, mean 16, gamma 2.1; one C6 and one
-# glasses colouring): the closure 24.48 GB / 13.01 GB, the leaf joins and
-# the triangle list as set below.  The bench multiplies them by the full
-# workload's algorithmic bytes.  The small case's tables fit in L2, so the
-# leaf-join and triangle ratios are lower bounds.
-TRAFFIC_PER_ALG_BYTE = {"cycle_closure": 24.48 / 13.01, "leaf_join": None, "triangle": None}
+# glasses colouring): the closure 24.48 GB / 13.01 GB, the leaf joins
+# (lanes on the output slots) 88.6 MB / 978 MB, the triangle list 104.2 MB /
+# 494 MB.  The bench multiplies them by the full workload's algorithmic
+# bytes.  The small case's tables fit in L2, so the leaf-join and triangle
+# ratios are lower bounds.
+TRAFFIC_PER_ALG_BYTE = {"cycle_closure": 24.48 / 13.01, "leaf_join": 88.6 / 978.0, "triangle": 104.2 / 493.6}
 FLUSH_BYTES = 256 << 20
 # CPU baseline: whole colourings on a smaller graph of the benchmark's shape
 CPU_GRAPH = {"graph": "chung_lu", "n": 2_000, "mean_deg": 16, "gamma": 2.1, "seed": 2}
