@@ -27,7 +27,7 @@ VARIANTS = {
     # the per-CTA push's bounded wait gives up on its first entry
     "libcc_waittest.so": (("cycle_plain.cu", "noalloc.cu"), ("-DCC_TEST_WAIT_EXPIRES",)),
     # data-dependent indices checked against their arrays (status flag, access skipped)
-    "libcc_boundscheck.so": (("cycle_plain.cu", "triangle.cu", "join.cu"), ("-DCC_BOUNDS_CHECK",)),
+    "libcc_boundscheck.so": (("cycle_plain.cu", "triangle.cu", "join.cu", "cycle.cu"), ("-DCC_BOUNDS_CHECK",)),
 }
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
          "-I" + os.path.join(ROOT, "include")]

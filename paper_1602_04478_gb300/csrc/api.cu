@@ -141,6 +141,7 @@ TabE tab_e(const std::vector<Table> &T, int idx, bool use_rev) {
   if (T[idx].pair) {
     t.gi = idx;
     t.ridx = T[idx].pg.ridx;
+    t.nrows = T[idx].pg.n_pairs;
   }
   return t;
 }

@@ -34,6 +34,7 @@ struct TabE {
   bool use_rev = false;
   int gi = -1;
   const int64_t *ridx = nullptr;
+  int64_t nrows = 0;  // rows behind ridx (bounds-check build)
 };
 
 struct LeafArgs {

@@ -105,9 +105,10 @@ __device__ __forceinline__ GraphView walk_graph(const CycleArgs &a, const TabE &
 }
 
 // Row of an edge-keyed table for walk position epos (null: all zero).
-__device__ __forceinline__ const u64 *erow_of(const TabE &E, int64_t epos) {
+__device__ __forceinline__ const u64 *erow_of(const TabE &E, int64_t epos, unsigned long long *status) {
   if (!E.ridx) return E.p + epos * E.R;
   const int64_t r = __ldg(E.ridx + epos);
+  if (r >= 0 && E.nrows > 0 && !cc_in(r, E.nrows, status)) return nullptr;
   return r < 0 ? nullptr : E.p + r * E.R;
 }
 
@@ -167,7 +168,8 @@ __device__ void join_node(const Lut &lut, const u64 *in, int s_in, int R_in, con
 
 // dst (pair row (u, y), size s_in + E.s - 1) += extend(src pair row (u, x) over edge x -> y)
 __device__ __forceinline__ void extend_row(const Lut &lut, const u64 *src, int s_in, int R_in, const TabE &E,
-                                           int64_t epos, int cu, int cx, int cy, u64 *dst, unsigned &ovf) {
+                                           int64_t epos, int cu, int cx, int cy, u64 *dst, unsigned &ovf,
+                                           unsigned long long *status) {
   if (!E.p) {
     if (cy == cx) return;
     for (int j = 0; j < R_in; j++) {
@@ -179,7 +181,7 @@ __device__ __forceinline__ void extend_row(const Lut &lut, const u64 *src, int s
     }
     return;
   }
-  const u64 *erow = erow_of(E, epos);
+  const u64 *erow = erow_of(E, epos, status);
   if (!erow) return;
   for (int l = 0; l < E.R; l++) {
     u64 t = __ldg(erow + l);
@@ -234,7 +236,9 @@ __device__ __forceinline__ void pull_hop(const CycleArgs &a, const GraphView &gg
       atomic_add_ck(acc + pslot(a.lut, (1u << cu) | (1u << cx), cu, cx), 1ull, ovf);
       return;
     }
-    const u64 *er = erow_of(last.E, last.E.use_rev ? e : __ldg(gg.rev + e));
+    const int64_t ep0 = last.E.use_rev ? e : __ldg(gg.rev + e);
+    if (!cc_in(ep0, gg.nnz, a.status)) return;
+    const u64 *er = erow_of(last.E, ep0, a.status);
     if (!er) return;
     for (int l = 0; l < last.E.R; l++) {
       const u64 t = __ldg(er + l);
@@ -245,8 +249,9 @@ __device__ __forceinline__ void pull_hop(const CycleArgs &a, const GraphView &gg
   }
   if (!stamp_has(P.stamp, w, cur, hs * kMaxLevels + lv)) return;
   const int64_t ep = last.E.p ? (last.E.use_rev ? e : __ldg(gg.rev + e)) : 0;
+  if (last.E.p && !cc_in(ep, gg.nnz, a.status)) return;
   extend_row(a.lut, P.rows[hs][lv] + (int64_t)w * sc.rstride[hs][lv], s_prev, R_prev, last.E, ep, cu, cw, cx, acc,
-             ovf);
+             ovf, a.status);
 }
 
 // MB: resident CTAs per SM the register allocation is held to.  Launches
@@ -319,7 +324,8 @@ __global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScr
         const int64_t ub = hf == 0 ? ub0 : ub1;
         const int du = hf == 0 ? du0 : du1;
         for (int i = tid; i < du; i += kCtaThreads) {
-          const int32_t v = __ldg(gf.col + ub + i);
+          int32_t v = __ldg(gf.col + ub + i);
+          if (!cc_in(v, a.g.n, a.status)) v = u;  // (bounds-check build) recorded, then skipped as u's colour
           const int cv = a.colors[v];
           P.list[hf][1][i] = v;
           stamp_set(P.stamp, v, cur, hf * kMaxLevels + 1);
@@ -331,7 +337,9 @@ __global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScr
           const TabE &E = li.E;
           const u64 *erow = nullptr;
           if (E.p) {
-            erow = erow_of(E, E.use_rev ? __ldg(gf.rev + ub + i) : ub + i);
+            const int64_t ep1 = E.use_rev ? __ldg(gf.rev + ub + i) : ub + i;
+            if (!cc_in(ep1, gf.nnz, a.status)) continue;
+            erow = erow_of(E, ep1, a.status);
             if (!erow) continue;
           }
           const u64 *nrow = (hf == 1 && a.N[h].p) ? a.N[h].p + (int64_t)u * a.N[h].R : nullptr;
@@ -396,13 +404,15 @@ __global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScr
             const int64_t ve = row_end(a, gw, vb, v, u);
             for (int64_t e = vb + lane; e < ve; e += 32) {
               const int32_t w = __ldg(gw.col + e);
+              if (!cc_in(w, a.g.n, a.status)) continue;
               if (stamp_set(P.stamp, w, cur, hf * kMaxLevels + j + 1)) {
                 int slot = atomicAdd(&s_cnt[hf * kMaxLevels + j + 1], 1);
                 P.list[hf][j + 1][slot] = w;
               }
               int64_t epos = ln.E.use_rev ? __ldg(gw.rev + e) : e;
+              if (ln.E.p && !cc_in(epos, gw.nnz, a.status)) continue;
               extend_row(a.lut, src, lj.s, Rj, ln.E, epos, cu, cv, a.colors[w], dstbase + (int64_t)w * dstride,
-                         ovf);
+                         ovf, a.status);
             }
           }
         }
@@ -472,6 +482,7 @@ __global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScr
           const int64_t ve = row_end(a, gc, vb, v, u);
           for (int64_t e = vb + lane; e < ve; e += 32) {
             const int32_t x = __ldg(gc.col + e);
+            if (!cc_in(x, a.g.n, a.status)) continue;
             if (stamp_set(P.stamp, x, cur, 2 * kMaxLevels)) {
               int slot = atomicAdd(&s_cnt[2 * kMaxLevels], 1);
               P.xlist[slot] = x;
@@ -500,6 +511,7 @@ __global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScr
             const int64_t xe = row_end(a, gP, xb, x, u);
             for (int64_t e = xb + lane; e < xe; e += 32) {
               const int32_t w = __ldg(gP.col + e);
+              if (!cc_in(w, a.g.n, a.status)) continue;
               const int cw = a.colors[w];
               pull_hop(a, gP, P, sc, cur, hp, rp - 1, lp_last, sPprev, RPprev, e, w, cw, u, cu, cx, accP, ovf);
               if (one_walk)
@@ -510,6 +522,7 @@ __global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScr
               const int64_t me = row_end(a, gM, mb, x, u);
               for (int64_t e = mb + lane; e < me; e += 32) {
                 const int32_t w = __ldg(gM.col + e);
+                if (!cc_in(w, a.g.n, a.status)) continue;
                 pull_hop(a, gM, P, sc, cur, hm, rm - 1, lm_last, lm_prev.s, RMprev, e, w, a.colors[w], u, cu, cx,
                          accM, ovf);
               }
