@@ -123,11 +123,14 @@ int cc_graph_info(cc_ctx *ctx, int32_t graph_id, int64_t *n, int64_t *nnz, int64
  * connected.  The library decomposes it into blocks (Section 4.1: leaf
  * edges and induced cycles with at most two boundary nodes, contracted by
  * Cases 1-3) and computes aut(Q) by enumeration.  CC_ERR_NOT_TW2 when no
- * decomposition exists (Lemma 4.1), CC_ERR_UNSUPPORTED when every
- * decomposition needs a non-root cycle block longer than a triangle with two
- * boundary nodes (Case 2), or a cycle longer than 8.  Non-root cycles of
- * length >= 4 with one boundary node (Case 1) are built from the general
- * per-source kernel rooted at the boundary node (no vertex order). */
+ * decomposition exists (Lemma 4.1), CC_ERR_UNSUPPORTED when no
+ * decomposition can run (cc_plan_supported: a cycle longer than 8, a Case-2
+ * cycle whose longer side between its boundary nodes has more than 5 edges).
+ * Non-root cycles of length >= 4 are built from the general per-source
+ * kernel without vertex order: with one boundary node (Case 1) rooted there,
+ * with two (Case 2) cut at both, their table keyed by data edges when the
+ * boundary pair is joined by one, else by the nonzero pairs (a pair graph
+ * the parent block walks). */
 int cc_set_query(cc_ctx *ctx, int k, int n_edges, const int32_t *edges, int32_t *query_id);
 
 /* Replace the query's decomposition by an explicit contraction order.
@@ -216,7 +219,11 @@ int cc_count(cc_ctx *ctx, int32_t graph_id, int32_t query_id, int first_trial, i
  * (sum of `trials` entries, UINT64_MAX for an overflowing trial); status
  * (nullable, n_reqs entries) receives CC_OK or CC_ERR_OVERFLOW per request.
  * Counts are identical to cc_count's.  Returns CC_OK unless a request is
- * invalid or a CUDA / memory error occurs. */
+ * invalid or a CUDA / memory error occurs.  A plan with a Case-2 block whose
+ * table is keyed by pairs that need not be data edges sizes that table on
+ * the host during the pass (a device-to-host read of its length): a batch
+ * holding such a plan runs its passes with those synchronisations and is
+ * not recorded as a CUDA graph. */
 typedef struct cc_request {
   int32_t graph_id;
   int32_t query_id;
