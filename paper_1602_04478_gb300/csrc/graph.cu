@@ -35,28 +35,30 @@ __device__ __forceinline__ unsigned long long sm64_mix(unsigned long long x) {
   return z ^ (z >> 31);
 }
 
-__global__ void k_degree_keys(int64_t n, const int64_t *row_ptr, unsigned long long *keys) {
+// Sort keys pack (major << bn) | minor, bn = the bits of a vertex id, so the
+// radix sorts cover only the bits in use.
+__global__ void k_degree_keys(int64_t n, const int64_t *row_ptr, unsigned long long *keys, int bn) {
   int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (v < n) keys[v] = ((unsigned long long)(row_ptr[v + 1] - row_ptr[v]) << 32) | (unsigned long long)v;
+  if (v < n) keys[v] = ((unsigned long long)(row_ptr[v + 1] - row_ptr[v]) << bn) | (unsigned long long)v;
 }
 
-__global__ void k_rank_of(int64_t n, const unsigned long long *sorted, int32_t *id_of, int32_t *rank_of) {
+__global__ void k_rank_of(int64_t n, const unsigned long long *sorted, int32_t *id_of, int32_t *rank_of, int bn) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r < n) {
-    int32_t v = (int32_t)(sorted[r] & 0xFFFFFFFFull);
+    int32_t v = (int32_t)(sorted[r] & ((1ull << bn) - 1ull));
     id_of[r] = v;
     rank_of[v] = (int32_t)r;
   }
 }
 
-// one warp per original row: edge keys (rank(src) << 32 | rank(dst)); also
+// one warp per original row: edge keys (rank(src) << bn | rank(dst)); also
 // flags ids out of range
 __global__ void k_edge_keys(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *rank_of,
-                            unsigned long long *keys, unsigned long long *status) {
+                            unsigned long long *keys, unsigned long long *status, int bn) {
   int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= n) return;
-  unsigned long long rs = (unsigned long long)rank_of[warp] << 32;
+  unsigned long long rs = (unsigned long long)rank_of[warp] << bn;
   for (int64_t e = row_ptr[warp] + lane; e < row_ptr[warp + 1]; e += 32) {
     int32_t c = col[e];
     if (c < 0 || c >= n) {
@@ -68,9 +70,15 @@ __global__ void k_edge_keys(int64_t n, const int64_t *row_ptr, const int32_t *co
   }
 }
 
-__global__ void k_split_keys(int64_t nnz, const unsigned long long *keys, int32_t *col) {
+__global__ void k_split_keys(int64_t nnz, const unsigned long long *keys, int32_t *col, int bn) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e < nnz) col[e] = (int32_t)(keys[e] & 0xFFFFFFFFull);
+  if (e < nnz) col[e] = (int32_t)(keys[e] & ((1ull << bn) - 1ull));
+}
+
+static int bits_for(unsigned long long x) {
+  int b = 1;
+  while (b < 63 && (x >> b) != 0ull) b++;
+  return b;
 }
 
 // warp per (rank-ordered) row: validity, lower-neighbour count, reverse edges
@@ -127,8 +135,13 @@ void graph_free(Ctx &c, DevGraph &g) {
 int graph_load(Ctx &c, int64_t n, const int64_t *row_ptr, const int32_t *col, int64_t nnz, DevGraph &g) {
   if (n <= 0 || n >= (int64_t)1 << 31 || nnz < 0 || !row_ptr || (nnz > 0 && !col)) return CC_ERR_INVALID_ARG;
   if (row_ptr[0] != 0 || row_ptr[n] != nnz) return CC_ERR_BAD_GRAPH;
-  for (int64_t v = 0; v < n; v++)
+  int64_t deg_max = 0;
+  for (int64_t v = 0; v < n; v++) {
     if (row_ptr[v + 1] < row_ptr[v]) return CC_ERR_BAD_GRAPH;
+    deg_max = std::max<int64_t>(deg_max, row_ptr[v + 1] - row_ptr[v]);
+  }
+  // key widths: vertex ids (and ranks) below 2^bn, degrees below 2^bd
+  const int bn = bits_for((unsigned long long)(n - 1)), bd = bits_for((unsigned long long)deg_max);
   cudaStream_t st = c.stream;
   g = DevGraph();
   g.n = n;
@@ -174,11 +187,11 @@ int graph_load(Ctx &c, int64_t n, const int64_t *row_ptr, const int32_t *col, in
       rc = CC_ERR_CUDA;
       break;
     }
-    k_degree_keys<<<blocks_for(n, 256), 256, 0, st>>>(n, d_rp, k0);
+    k_degree_keys<<<blocks_for(n, 256), 256, 0, st>>>(n, d_rp, k0, bn);
     c.kernels++;
     size_t tbx = tb;
-    if (cub::DeviceRadixSort::SortKeys(tmp, tbx, k0, k1, n, 0, 64, st) != cudaSuccess) { rc = CC_ERR_CUDA; break; }
-    k_rank_of<<<blocks_for(n, 256), 256, 0, st>>>(n, k1, g.id_of, g.rank_of);
+    if (cub::DeviceRadixSort::SortKeys(tmp, tbx, k0, k1, n, 0, bn + bd, st) != cudaSuccess) { rc = CC_ERR_CUDA; break; }
+    k_rank_of<<<blocks_for(n, 256), 256, 0, st>>>(n, k1, g.id_of, g.rank_of, bn);
     c.kernels++;
     // rank-ordered row pointers on the host (degrees are known there)
     std::vector<int32_t> id_of(n);
@@ -195,11 +208,11 @@ int graph_load(Ctx &c, int64_t n, const int64_t *row_ptr, const int32_t *col, in
       break;
     }
     if (nnz > 0) {
-      k_edge_keys<<<blocks_for(n * 32, 256), 256, 0, st>>>(n, d_rp, d_col, g.rank_of, k0, c.d_status);
+      k_edge_keys<<<blocks_for(n * 32, 256), 256, 0, st>>>(n, d_rp, d_col, g.rank_of, k0, c.d_status, bn);
       c.kernels++;
       tbx = tb;
-      if (cub::DeviceRadixSort::SortKeys(tmp, tbx, k0, k1, nnz, 0, 64, st) != cudaSuccess) { rc = CC_ERR_CUDA; break; }
-      k_split_keys<<<blocks_for(nnz, 256), 256, 0, st>>>(nnz, k1, g.col);
+      if (cub::DeviceRadixSort::SortKeys(tmp, tbx, k0, k1, nnz, 0, 2 * bn, st) != cudaSuccess) { rc = CC_ERR_CUDA; break; }
+      k_split_keys<<<blocks_for(nnz, 256), 256, 0, st>>>(nnz, k1, g.col, bn);
       c.kernels++;
     }
     k_finish_rows<<<blocks_for(n * 32, 256), 256, 0, st>>>(n, g.row, g.col, g.rev, g.lo_cnt, c.d_status);
