@@ -158,3 +158,46 @@ def test_pair_list_outgrows_the_previous_pass(cc):
     finally:
         P.cc_clear_colors(cc.h, gid)
         cc.free_graph(gid)
+
+
+@pytest.mark.parametrize("qname", ["theta_5_2", "theta_333", "theta_2233"])
+def test_per_vertex_split_of_a_root_reading_pairs(cc, qname):
+    """A root cycle that walks a pair graph (DB procedure): its count split by
+    the highest vertex equals the oracle's split for a tree with the same
+    root block."""
+    import paper_1602_04478_gb300 as P
+    k, e = QUERIES[qname]
+    g = GRAPHS["cl1000"]()
+    lib_root = P.cc_plan_inspect(k, e)[0][-1]
+    choice = None
+    for p in O.all_plans(k, e, limit=200):
+        blocks, root, _ = O.decompose(k, e, choice=p)
+        if blocks[root]["kind"] == "root_cycle" and sorted(blocks[root]["nodes"]) == sorted(lib_root["nodes"]):
+            choice = p
+            break
+    assert choice is not None
+    expect, _, per = O.dp_count(g, k, e, O.colors(6, 0, g.n, k), choice=choice, per_source=True)
+    gid = cc.load_graph(g)
+    try:
+        P.cc_set_coloring_seed(cc.h, 6)
+        qid = cc.set_query(k, e)
+        pv, total = cc.count_per_vertex(gid, qid, 0)
+        assert total == expect and [int(x) for x in pv] == per
+    finally:
+        cc.free_graph(gid)
+
+
+def test_per_vertex_refused_for_a_root_triangle_reading_pairs(cc):
+    """K_{2,3}'s root triangle reads a pair-keyed edge and runs without vertex
+    order, so its count has no split by the highest vertex."""
+    import paper_1602_04478_gb300 as P
+    k, e = QUERIES["K23"]
+    g = GRAPHS["er60"]()
+    gid = cc.load_graph(g)
+    try:
+        qid = cc.set_query(k, e)
+        with pytest.raises(P.CCError) as ei:
+            cc.count_per_vertex(gid, qid, 0)
+        assert P.ERRORS[ei.value.code] == "CC_ERR_UNSUPPORTED"
+    finally:
+        cc.free_graph(gid)
