@@ -701,17 +701,21 @@ def run_profile_case(args):
     ctx = P.Context(0, budget_bytes=int(args.profile_budget * (1 << 30)))
     gid = ctx.load_graph(g)
     P.cc_set_coloring_seed(ctx.h, COLOR_SEED)
-    # --profile-tuned: the benchmark's own choices (tuned threshold, measured tree)
-    hd = args.heavy_degree if args.heavy_degree >= 0 else (-1 if args.profile_tuned else 384)
+    hd = args.heavy_degree if args.heavy_degree >= 0 else 384
     P.cc_set_heavy_degree(ctx.h, hd)
-    out = {"profile_case": args.profile_case, "n": n, "mean_deg": mean, "heavy_degree": hd,
-           "tuned": args.profile_tuned, "budget_gib": args.profile_budget, "queries": {}}
+    # --profile-trees NAME=I,...: the I-th supported tree (cc_autotune_plan's
+    # index, as the benchmark line reports it) instead of the default tree;
+    # timing the trees under a profiler would mislead the choice
+    trees = dict((kv.split("=")[0], int(kv.split("=")[1])) for kv in args.profile_trees.split(",") if kv)
+    out = {"profile_case": args.profile_case, "n": n, "mean_deg": mean, "heavy_degree": hd, "trees": trees,
+           "budget_gib": args.profile_budget, "queries": {}}
     for name in args.profile_case.split(","):
-        q = ctx.set_query(*(CASE2_QUERIES[name] if name in CASE2_QUERIES else gg.query(name)))
-        if args.profile_tuned:
-            if hd < 0:
-                P.cc_autotune(ctx.h, gid, q)
-            P.cc_autotune_plan(ctx.h, gid, q)
+        k, e = CASE2_QUERIES[name] if name in CASE2_QUERIES else gg.query(name)
+        q = ctx.set_query(k, e)
+        if name in trees:
+            seq = [t for t in P.cc_plan_enumerate(k, e) if t["supported"]][trees[name]]["seq"]
+            if seq:
+                P.cc_set_decomposition(ctx.h, q, seq)
         detail = P.cc_work_detail(ctx.h, gid, q)
         ctx.count(gid, q, 100, 1, allow_overflow=True)  # per-graph structure, outside the captured launches
         cols = [int(ctx.count(gid, q, t, 1, allow_overflow=True)[0][0]) for t in range(args.profile_reps)]
@@ -744,8 +748,8 @@ def main():
     ap.add_argument("--profile-n", type=int, default=0, help="graph size of --profile-case (0: the benchmark's)")
     ap.add_argument("--profile-mean", type=float, default=0, help="mean degree of --profile-case (0: 16)")
     ap.add_argument("--profile-reps", type=int, default=1, help="colourings counted by --profile-case")
-    ap.add_argument("--profile-tuned", action="store_true",
-                    help="--profile-case with the benchmark's tuned threshold and measured tree")
+    ap.add_argument("--profile-trees", default="",
+                    help="NAME=I,...: --profile-case counts NAME with its I-th supported tree")
     ap.add_argument("--profile-budget", type=float, default=0,
                     help="device memory budget of --profile-case in GiB (0: none); caps the per-CTA push's slots")
     ap.add_argument("--rmat-pendants", action="store_true",
