@@ -76,3 +76,36 @@ def test_random_query_every_tree(cc, graph_and_id, seed):
             P.cc_set_decomposition(cc.h, qid, t["seq"])
         got = int(cc.count(gid, qid, 0, 1)[0][0])
         assert got == want, (k, e, t["seq"])
+
+
+@pytest.fixture(scope="module")
+def power_law(cc):
+    g = gg.chung_lu(1500, 6, 2.1, 23)
+    gid = cc.load_graph(g)
+    yield g, gid
+    cc.free_graph(gid)
+
+
+@pytest.mark.parametrize("seed", list(range(200, 230)))
+def test_random_query_power_law_heavy_paths(cc, power_law, seed):
+    """The same on a heavy-tailed graph with the heavy-source threshold at
+    degree 24, so root cycles also take the grouped heavy paths (plain and
+    annotated) beside the per-CTA ones."""
+    import paper_1602_04478_gb300 as P
+    g, gid = power_law
+    k, e = random_sp_query(seed, 8)
+    trees = [t for t in P.cc_plan_enumerate(k, e) if t["supported"]]
+    rng = np.random.default_rng(seed)
+    pick = trees if len(trees) <= 3 else [trees[i] for i in sorted(rng.choice(len(trees), 3, replace=False))]
+    want = O.dp_count(g, k, e, O.colors(seed, 0, g.n, k))[0]
+    P.cc_set_coloring_seed(cc.h, seed)
+    P.cc_set_heavy_degree(cc.h, 24)
+    try:
+        for t in pick:
+            qid = cc.set_query(k, e)
+            if t["seq"]:
+                P.cc_set_decomposition(cc.h, qid, t["seq"])
+            got = int(cc.count(gid, qid, 0, 1)[0][0])
+            assert got == want, (k, e, t["seq"])
+    finally:
+        P.cc_set_heavy_degree(cc.h, -1)
