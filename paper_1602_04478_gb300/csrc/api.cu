@@ -434,6 +434,104 @@ int run_triangle_on_cycle(Ctx &c, const GraphView &gv, const Lut &lut, const uin
   return rc;
 }
 
+// The block's tables on the cycle in the order a_0 = nodes[p0], a_1, ...
+// (reflect: a_0 = nodes[p0], a_1 = nodes[p0 - 1], ...).
+void orient_cycle(CycleArgs &a, const Stage &st, const std::vector<Table> &T, int p0, bool reflect) {
+  const int L = st.L;
+  for (int j = 0; j < L; j++) {
+    if (!reflect) {
+      const int o = (j + p0) % L;  // node j is nodes[o]; edge j joins nodes[o] -> nodes[o+1]
+      a.N[j] = tab_u(T, st.node_child[o]);
+      a.Efw[j] = tab_e(T, st.edge_child[o], !st.edge_fwd[o]);
+      a.Ebw[j] = tab_e(T, st.edge_child[o], st.edge_fwd[o]);
+    } else {
+      const int o = (p0 - j + L) % L;           // node j is nodes[o]
+      const int eo = (p0 - j - 1 + 2 * L) % L;  // edge j joins nodes[o] -> nodes[o-1]: edge eo backwards
+      a.N[j] = tab_u(T, st.node_child[o]);
+      a.Efw[j] = tab_e(T, st.edge_child[eo], st.edge_fwd[eo]);
+      a.Ebw[j] = tab_e(T, st.edge_child[eo], !st.edge_fwd[eo]);
+    }
+  }
+}
+
+// Case-1 block of length L >= 4 (one boundary node b): its unary table
+// cnt(v, alpha | B) by the image v of b.
+//   PS: the cycle rotated so b is a_0, one split at a_0 and its opposite
+//       node, no vertex order (every image of b a source).
+//   DB (Eq. 1 over the block): for each node a_h as the highest, paths below
+//       its image u, cut at a_h and at b: for h = b the row is u's; for
+//       any other h the cut node b is the meeting vertex x and the row is
+//       x's.  The forward distance f from a_h to b sets P+'s length; where f
+//       exceeds L/2 the cycle is walked the other way (a second launch with
+//       the reflected order), so both halves keep at least two hops.  A cut
+//       next to b leaves a half of L - 1 hops, so L <= 6 (longer: PS).
+int run_case1(Ctx &c, const GraphView &gv, const Lut &lut, const uint8_t *colors, int k, const Stage &st,
+              std::vector<Table> &T, size_t i, u64 *status, bool count_units) {
+  const int L = st.L;
+  int p0 = 0;
+  while (p0 < L && st.nodes[p0] != st.bd[0]) p0++;
+  if (p0 == L) return CC_ERR_INVALID_ARG;
+  auto base = [&](bool reflect) {
+    CycleArgs a;
+    a.g = gv;
+    a.colors = colors;
+    a.k = k;
+    a.lut = lut;
+    a.L = L;
+    orient_cycle(a, st, T, p0, reflect);
+    a.multiplier = 1;
+    a.per_vertex = nullptr;
+    a.status = status;
+    a.count_units = count_units;
+    a.out_mode = 1;
+    a.out = T[i].p;
+    a.R_out = T[i].R;
+    a.s_out = st.s;
+    return a;
+  };
+  int rc = CC_OK;
+  // DB cuts next to b leave a half of L - 1 hops: longer cycles take PS
+  if (c.procedure == CC_PROC_PS || L - 1 > kMaxHalf) {
+    CycleArgs a = base(false);
+    a.no_order = true;
+    a.n_h = 1;
+    a.hs[0] = 0;
+    if ((rc = bind_pairs(a, T)) != CC_OK) return rc;
+    rc = launch_cycle(c, a);
+    if (rc != CC_OK) c.scratch_dirty = c.hv_dirty = true;
+    return rc;
+  }
+  // DB: h = 0 and the h whose forward distance L - h to b is at most L/2 in
+  // this order; the others (1 <= h < L - L/2) reflected, where b lies h ahead
+  CycleArgs fw = base(false), bw = base(true);
+  fw.no_order = bw.no_order = false;
+  fw.out_atomic = bw.out_atomic = true;
+  fw.n_h = bw.n_h = 0;
+  for (int h = 0; h < L; h++) {
+    if (h == 0) {
+      fw.hs[fw.n_h++] = 0;  // b highest: u's row, the usual opposite cut
+    } else if (L - h <= L / 2) {
+      fw.split_h[h] = L - h;
+      fw.out_key_x[fw.n_h] = true;
+      fw.hs[fw.n_h++] = h;
+    } else {
+      const int hr = L - h;  // a_h in the reflected order
+      bw.split_h[hr] = h;
+      bw.out_key_x[bw.n_h] = true;
+      bw.hs[bw.n_h++] = hr;
+    }
+  }
+  for (CycleArgs *a : {&fw, &bw}) {
+    if (a->n_h == 0) continue;
+    if ((rc = bind_pairs(*a, T)) != CC_OK) return rc;
+    if ((rc = launch_cycle(c, *a)) != CC_OK) {
+      c.scratch_dirty = c.hv_dirty = true;
+      return rc;
+    }
+  }
+  return rc;
+}
+
 // Issue one colouring pass of the plan on the context's stream: status words
 // zeroed, colours, every block bottom-up into its table, the root into
 // status[ST_COUNT] (and d_per_vertex, rank order, when given).  No host
@@ -591,40 +689,7 @@ int enqueue_pass(Ctx &c, DevGraph &g, const Plan &p, int64_t trial, PassBuffers 
     } else if (st.kind == ST_CYCLE_NONROOT && st.nb == 2) {
       rc = run_case2(c, g, gv, lut, B.colors, k, st, T, i, status, count_units);
     } else if (st.kind == ST_CYCLE_NONROOT && st.nb == 1) {
-      // Case 1 block, L >= 4: its unary table by the image of the boundary
-      // node, from the general kernel rooted there -- the cycle rotated so
-      // the boundary node is a_0, one split at a_0 and its opposite node,
-      // no vertex order (the image of a_0 is fixed, not the highest)
-      const int L = st.L;
-      int p0 = 0;
-      while (p0 < L && st.nodes[p0] != st.bd[0]) p0++;
-      if (p0 == L) { rc = CC_ERR_INVALID_ARG; break; }
-      CycleArgs a;
-      a.g = gv;
-      a.colors = B.colors;
-      a.k = k;
-      a.lut = lut;
-      a.L = L;
-      for (int j = 0; j < L; j++) {
-        const int o = (j + p0) % L;
-        a.N[j] = tab_u(T, st.node_child[o]);
-        a.Efw[j] = tab_e(T, st.edge_child[o], !st.edge_fwd[o]);
-        a.Ebw[j] = tab_e(T, st.edge_child[o], st.edge_fwd[o]);
-      }
-      a.no_order = true;
-      a.n_h = 1;
-      a.hs[0] = 0;
-      a.multiplier = 1;
-      a.per_vertex = nullptr;
-      a.status = status;
-      a.count_units = count_units;
-      a.out_mode = 1;
-      a.out = T[i].p;
-      a.R_out = R;
-      a.s_out = st.s;
-      if ((rc = bind_pairs(a, T)) != CC_OK) break;
-      rc = launch_cycle(c, a);
-      if (rc != CC_OK) c.scratch_dirty = c.hv_dirty = true;
+      rc = run_case1(c, gv, lut, B.colors, k, st, T, i, status, count_units);
     } else if (st.kind == ST_ROOT_NODE) {
       const Table &ct = T[st.node_child[0]];
       if (ct.R != 1) { rc = CC_ERR_INVALID_ARG; break; }

@@ -101,8 +101,10 @@ struct CycleArgs {
   bool count_units = false;   // add the structural edge-subset work to status[ST_UNITS]
   int32_t light_end = 0;      // the per-CTA kernel takes sources of rank < light_end
   bool no_order = false;      // PS procedure: paths from u are not restricted to vertices below u
-  // length of P+ (the cut nodes are a_h and a_{h+split}); 0: floor(L/2)
+  // length of P+ (the cut nodes are a_h and a_{h+split}); 0: floor(L/2);
+  // split_h[h] != 0 overrides it for highest node h
   int split = 0;
+  int split_h[kMaxCycle] = {0, 0, 0, 0, 0, 0, 0, 0};
   // pair graphs of the pair-keyed edge tables (TabE::gi)
   GraphView pg[kMaxPairGraphs];
   // Non-root cycle (no_order, the first boundary node at position 0, its
@@ -114,6 +116,13 @@ struct CycleArgs {
   //               appended to pair_keys (u << 32 | x) / pair_rows [][R_out]
   //               (pair_keys null: only counted into *pair_count)
   int out_mode = 0;
+  // out_mode 1 under DB (Case 1 with the highest node not the boundary):
+  // out_key_x[hi], the row of highest-node choice hs[hi] is the meeting
+  // vertex x's (the boundary node is the cut node a_{h+split}), added by
+  // atomics; out_atomic, u's rows are added rather than stored (other CTAs
+  // add to them too)
+  bool out_key_x[kMaxCycle] = {false, false, false, false, false, false, false, false};
+  bool out_atomic = false;
   u64 *out = nullptr;
   int R_out = 0, s_out = 0;
   unsigned long long *pair_keys = nullptr;

@@ -57,11 +57,16 @@ struct LevelInfo {
   TabE E;
 };
 
+// Length of P+ for highest node h.
+__device__ __host__ inline int split_of(const CycleArgs &a, int h) {
+  return a.split_h[h] ? a.split_h[h] : (a.split ? a.split : a.L / 2);
+}
+
 // Sizes and tables of level j (1..depth) of half `half` for highest node h.
 __device__ __host__ inline void level_info(const CycleArgs &a, int h, int half, int j, LevelInfo &out,
                                            int *depth_out) {
   int L = a.L;
-  int rp = a.split ? a.split : L / 2, rm = L - rp;
+  int rp = split_of(a, h), rm = L - rp;
   int depth = half == 0 ? rp : rm;
   if (depth_out) *depth_out = depth;
   int s = half == 0 ? 1 : (a.N[h].p ? a.N[h].s : 1);
@@ -229,29 +234,35 @@ __device__ __forceinline__ void pull_hop(const CycleArgs &a, const GraphView &gg
                                          const CycleScratch &sc, unsigned long long cur, int hs, int lv,
                                          const LevelInfo &last, int s_prev, int R_prev, int64_t e, int32_t w,
                                          int cw, int32_t u, int cu, int cx, u64 *acc, unsigned &ovf) {
-  // traversal w -> x: its CSR position is rev[e]
-  if (lv == 0) {
-    if (w != u) return;
-    if (!last.E.p) {
-      atomic_add_ck(acc + pslot(a.lut, (1u << cu) | (1u << cx), cu, cx), 1ull, ovf);
-      return;
-    }
-    const int64_t ep0 = last.E.use_rev ? e : __ldg(gg.rev + e);
-    if (!cc_in(ep0, gg.nnz, a.status)) return;
-    const u64 *er = erow_of(last.E, ep0, a.status);
-    if (!er) return;
-    for (int l = 0; l < last.E.R; l++) {
-      const u64 t = __ldg(er + l);
-      if (!t) continue;
-      atomic_add_ck(acc + pslot(a.lut, pmask(a.lut, last.E.s, l, cu, cx), cu, cx), t, ovf);
-    }
-    return;
-  }
+  // traversal w -> x: its CSR position is rev[e].  A half of one edge (lv
+  // 0) is added once per x by edge_hop instead.
+  if (lv == 0) return;
   if (!stamp_has(P.stamp, w, cur, hs * kMaxLevels + lv)) return;
   const int64_t ep = last.E.p ? (last.E.use_rev ? e : __ldg(gg.rev + e)) : 0;
   if (last.E.p && !cc_in(ep, gg.nnz, a.status)) return;
   extend_row(a.lut, P.rows[hs][lv] + (int64_t)w * sc.rstride[hs][lv], s_prev, R_prev, last.E, ep, cu, cw, cx, acc,
              ovf, a.status);
+}
+
+// P+ of a single edge u -> x (split 1): its row at x, from x's position in
+// u's row of the hop's graph (x was found there), added by one lane.
+__device__ __forceinline__ void edge_hop(const CycleArgs &a, const GraphView &gg, const LevelInfo &last, int32_t u,
+                                         int cu, int32_t x, int cx, u64 *acc, unsigned &ovf) {
+  const int64_t ub = gg.row[u], ue = gg.row[u + 1];
+  const int64_t q = lower_bound_i32(gg.col, ub, ue, x);
+  if (q >= ue || __ldg(gg.col + q) != x) return;
+  if (!last.E.p) {
+    atomic_add_ck(acc + pslot(a.lut, (1u << cu) | (1u << cx), cu, cx), 1ull, ovf);
+    return;
+  }
+  const int64_t ep = last.E.use_rev ? __ldg(gg.rev + q) : q;
+  if (!cc_in(ep, gg.nnz, a.status)) return;
+  const u64 *er = erow_of(last.E, ep, a.status);
+  if (!er) return;
+  for (int l = 0; l < last.E.R; l++) {
+    const u64 t = __ldg(er + l);
+    if (t) atomic_add_ck(acc + pslot(a.lut, pmask(a.lut, last.E.s, l, cu, cx), cu, cx), t, ovf);
+  }
 }
 
 // MB: resident CTAs per SM the register allocation is held to.  Launches
@@ -278,7 +289,6 @@ __global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScr
   const int o_all = a.out_mode == 0 ? 0 : (a.out_mode == 1 ? a.R_out : kWarps * a.R_out);
   for (int i = tid; i < o_all; i += kCtaThreads) obase[i] = 0;
   unsigned ovf = 0;
-  const int rp = a.split ? a.split : L / 2, rm = L - rp;
   while (true) {
     if (tid == 0) {
       // once a count of this pass has exceeded 2^64-1 the result is fixed
@@ -295,6 +305,8 @@ __global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScr
     bool wrote = false;
     for (int hi = 0; hi < a.n_h; hi++) {
       const int h = a.hs[hi];
+      const int rp = split_of(a, h), rm = L - rp;
+      const bool key_x = a.out_mode == 1 && a.out_key_x[hi];
       LevelInfo f0, f1;
       level_info(a, h, 0, 1, f0, nullptr);
       level_info(a, h, 1, 1, f1, nullptr);
@@ -507,6 +519,7 @@ __global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScr
           for (int t = lane; t < RM; t += 32) accM[t] = 0;
           __syncwarp();
           if (cx != cu) {
+            if (rp == 1 && lane == 0) edge_hop(a, gP, lp_last, u, cu, x, cx, accP, ovf);
             const int64_t xb = gP.row[x];
             const int64_t xe = row_end(a, gP, xb, x, u);
             for (int64_t e = xb + lane; e < xe; e += 32) {
@@ -554,6 +567,13 @@ __global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScr
                     const uint32_t mm = pmask(a.lut, lm_last.s_pre, t2, cu, cx);
                     if ((m1 & mm) != ((1u << cu) | (1u << cx))) continue;
                     const u64 v = mul_ck(vpn, vm, ovf);
+                    if (key_x) {
+                      // the boundary node is a_d: x's row of the unary table
+                      const int slot = uslot(a.lut, m1 | mm, cx);
+                      if (!cc_in(slot, a.R_out, a.status)) continue;
+                      atomic_add_ck(a.out + (int64_t)x * a.R_out + slot, v, ovf);
+                      continue;
+                    }
                     const int slot = a.out_mode == 1 ? uslot(a.lut, m1 | mm, cu) : pslot(a.lut, m1 | mm, cu, cx);
                     if (!cc_in(slot, a.R_out, a.status)) continue;
                     const unsigned long long old = atomicAdd(orow + slot, v);
@@ -634,9 +654,11 @@ __global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScr
       __syncthreads();
     }
     if (a.out_mode == 1 && wrote) {
-      // u's row of the non-root block's table (only this CTA writes it)
+      // u's row of the non-root block's table (only this CTA writes it, or,
+      // under DB, other CTAs add to it by atomics too)
       for (int i = tid; i < a.R_out; i += kCtaThreads) {
-        a.out[(int64_t)u * a.R_out + i] = orow[i];
+        if (a.out_atomic) atomic_add_ck(a.out + (int64_t)u * a.R_out + i, orow[i], ovf);
+        else a.out[(int64_t)u * a.R_out + i] = orow[i];
         orow[i] = 0;
       }
     }
@@ -662,22 +684,26 @@ __global__ void __launch_bounds__(kCtaThreads, MB) k_cycle(CycleArgs a, CycleScr
 static CycleScratch plan_scratch(const CycleArgs &a, int slots) {
   CycleScratch sc;
   int L = a.L, k = a.k;
-  int rp = a.split ? a.split : L / 2, rm = L - rp;
   bool plain = true;
   for (int i = 0; i < L; i++) plain = plain && !a.N[i].p && !a.Efw[i].p && !a.Ebw[i].p;
   sc.shared_chain = plain;
-  int mat[2] = {rp - 1, rm - 1};
-  if (plain) {
-    mat[0] = std::max(rp - 1, rm - 1);
-    mat[1] = 0;
-  }
   for (int hf = 0; hf < 2; hf++)
     for (int l = 0; l < kMaxLevels; l++) sc.rstride[hf][l] = sc.pstride[hf][l] = 0;
   int acc = 1;
+  // levels each half materialises, the most over the highest-node choices
+  int mat[2] = {0, 0};
   for (int hi = 0; hi < a.n_h; hi++) {
     int h = a.hs[hi];
+    const int rp = split_of(a, h), rm = L - rp;
+    int mh[2] = {rp - 1, rm - 1};
+    if (plain) {
+      mh[0] = std::max(rp - 1, rm - 1);
+      mh[1] = 0;
+    }
+    mat[0] = std::max(mat[0], mh[0]);
+    mat[1] = std::max(mat[1], mh[1]);
     for (int hf = 0; hf < 2; hf++) {
-      for (int l = 1; l <= mat[hf]; l++) {
+      for (int l = 1; l <= mh[hf]; l++) {
         LevelInfo li;
         level_info(a, h, hf, l, li, nullptr);
         sc.rstride[hf][l] = std::max<int>(sc.rstride[hf][l], (int)binom(k - 2, li.s - 2));
@@ -715,13 +741,16 @@ size_t cycle_scratch_bytes(const CycleArgs &a, int slots) { return plan_scratch(
 int launch_cycle(Ctx &c, const CycleArgs &a_in) {
   // triangles come here only without vertex order (pair-keyed tables)
   if (a_in.L < 3 || (a_in.L == 3 && !a_in.no_order) || a_in.L > kMaxCycle) return CC_ERR_UNSUPPORTED;
-  // a split of one (P+ the single edge u -> x) needs the whole row of x: no vertex order
-  if (a_in.split < 0 || a_in.split >= a_in.L || (a_in.split == 1 && !a_in.no_order)) return CC_ERR_INVALID_ARG;
-  {
-    const int rp = a_in.split ? a_in.split : a_in.L / 2;
+  if (a_in.split < 0 || a_in.split >= a_in.L || a_in.n_h < 1 || a_in.n_h > a_in.L) return CC_ERR_INVALID_ARG;
+  for (int hi = 0; hi < a_in.n_h; hi++) {
+    // P- has at least two hops (its first level carries a_h's block); both fit the level arrays
+    const int h = a_in.hs[hi];
+    if (h < 0 || h >= a_in.L || a_in.split_h[h] < 0 || a_in.split_h[h] >= a_in.L) return CC_ERR_INVALID_ARG;
+    const int rp = split_of(a_in, h);
+    if (a_in.L - rp < 2) return CC_ERR_INVALID_ARG;
     if (rp > kMaxLevels || a_in.L - rp > kMaxLevels) return CC_ERR_UNSUPPORTED;
   }
-  if (a_in.out_mode < 0 || a_in.out_mode > 3 || (a_in.out_mode && !a_in.no_order) ||
+  if (a_in.out_mode < 0 || a_in.out_mode > 3 || (a_in.out_mode >= 2 && !a_in.no_order) ||
       (a_in.out_mode == 2 && a_in.split != 1) || (a_in.out_mode == 3 && !a_in.pair_count))
     return CC_ERR_INVALID_ARG;
   CycleArgs a = a_in;
