@@ -82,7 +82,8 @@ int cc_set_memory_budget(cc_ctx *ctx, size_t bytes);
  * changes only the speed, never the counts. */
 int cc_set_heavy_degree(cc_ctx *ctx, int degree);
 
-/* Procedure for root cycle blocks of length >= 4 (Section 5).
+/* Procedure for root cycle blocks of length >= 4 and for non-root cycle
+ * blocks of length 4-6 with one boundary node (Section 5).
  * CC_PROC_DB (default): the degree-based procedure -- matches split by the
  * cycle node holding the highest vertex in the degree order (Eq. 1), paths
  * extended only through lower vertices (Procedures 1-2, general-cycle
@@ -91,8 +92,11 @@ int cc_set_heavy_degree(cc_ctx *ctx, int degree);
  * through any vertex (Procedures 1-2 of the PS algorithm figure).  Both give
  * the same counts; PS does far more work on skewed graphs and runs on the
  * library's general per-source kernel only.  cc_count_per_vertex splits a
- * PS count by the image of a_0.  Triangle and leaf blocks are the same under
- * both. */
+ * PS count by the image of a_0.  A non-root cycle with one boundary node b
+ * under DB: each node as the highest, cut there and at b; under PS (and for
+ * cycles of 7 or 8 nodes): one split at b and its opposite node, no order.
+ * Triangle and leaf blocks, and non-root cycles with two boundary nodes
+ * (cut at both, no order), are the same under both. */
 /* Triangle blocks (enable = 1, the default): the graph's triangles are
  * listed once, on the first count of a query with a triangle block (every
  * triangle u > v > w in the degree order, with the positions of its edges;
@@ -127,10 +131,10 @@ int cc_graph_info(cc_ctx *ctx, int32_t graph_id, int64_t *n, int64_t *nnz, int64
  * decomposition can run (cc_plan_supported: a cycle longer than 8, a Case-2
  * cycle whose longer side between its boundary nodes has more than 5 edges).
  * Non-root cycles of length >= 4 are built from the general per-source
- * kernel without vertex order: with one boundary node (Case 1) rooted there,
- * with two (Case 2) cut at both, their table keyed by data edges when the
- * boundary pair is joined by one, else by the nonzero pairs (a pair graph
- * the parent block walks). */
+ * kernel: with one boundary node (Case 1) by the procedure cc_set_procedure
+ * selects; with two (Case 2) cut at both without vertex order, their table
+ * keyed by data edges when the boundary pair is joined by one, else by the
+ * nonzero pairs (a pair graph the parent block walks). */
 int cc_set_query(cc_ctx *ctx, int k, int n_edges, const int32_t *edges, int32_t *query_id);
 
 /* Replace the query's decomposition by an explicit contraction order.
