@@ -3,11 +3,11 @@ parity cases: every index the benchmark-path kernels read from data -- CSR
 entries, level lists and local indices of the plain-cycle closure, triangle
 records and edge positions, leaf-join neighbours and slots, and in the
 general cycle kernel the neighbours, table positions and pair-table rows of
-every walk (data graph or pair graph) -- is checked
-against its array; a violation sets a status flag (the access is skipped)
-and the count returns CC_ERR_BOUNDS.  compute-sanitizer is closed on this
-pool; this build stands in for it.  Every case must come back CC_OK with the
-oracle's count."""
+every walk (data graph or pair graph) -- is checked against its array; a
+violation sets a status flag (the access is skipped) and the count returns
+CC_ERR_BOUNDS.  The build stands in for a memory checker such as
+compute-sanitizer, which these tests do not run.  Every case must come back
+CC_OK with the oracle's count."""
 import ctypes
 
 import numpy as np
